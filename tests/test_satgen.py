@@ -1,0 +1,49 @@
+"""The seeded instance generator: planted, unique, deterministic."""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import satgen
+
+
+@pytest.mark.parametrize("n,seed", [(6, 0), (9, 4), (12, 0), (14, 7)])
+def test_planted_unique_and_checked_by_oracle(n, seed):
+    inst = satgen.planted_instance(n, seed)
+    e = oracle.violated_counts(n, inst["clauses"])
+    assert np.flatnonzero(e == 0).tolist() == [inst["planted"]]
+    # the instance is minimal: dropping the last clause leaves >1 solution
+    assert oracle.count_solutions(n, inst["clauses"][:-1]) > 1
+    keys = {tuple(sorted(c)) for c in inst["clauses"]}
+    assert len(keys) == len(inst["clauses"])
+    for c in inst["clauses"]:
+        assert len({abs(l) for l in c}) == 3 and all(1 <= abs(l) <= n for l in c)
+
+
+def test_deterministic_and_methods_agree():
+    for n in (10, 15):
+        a = satgen.planted_instance(n, 3, method="incremental")
+        b = satgen.planted_instance(n, 3, method="chunked")
+        assert a == b
+        assert a == satgen.planted_instance(n, 3)
+
+
+def test_committed_instances_are_generator_output():
+    d = satgen.INSTANCE_DIR
+    path = os.path.join(d, "planted_n12_s0.json")
+    if not os.path.exists(path):
+        pytest.skip("instances not generated")
+    assert satgen.load_instance(path) == satgen.planted_instance(12, 0)
+    big = satgen.load_instance(os.path.join(d, "planted_n20_s0.json"))
+    assert big == satgen.planted_instance(20, 0)
+    assert oracle.count_solutions(20, big["clauses"]) == 1
+
+
+def test_serving_requests_shape():
+    reqs = satgen.serving_requests(64, seed=0, rate=100.0)
+    assert len(reqs) == 64
+    arr = [r[0] for r in reqs]
+    assert arr == sorted(arr)
+    assert all(10 <= r[1] <= 22 and 5.0 <= r[2] <= 80.0 for r in reqs)
