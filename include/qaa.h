@@ -1,0 +1,189 @@
+/*
+ * qaa.h -- C ABI of the GB300 adiabatic 3-SAT state-vector evolver.
+ *
+ * What it computes (the paper's method, restated):
+ *   Eq. (1)   H(s) = (1 - s) H_B + s H_P,  s = t / T, swept linearly over [0, 1].
+ *   Sec. 2.1  H_B is the beginning Hamiltonian whose ground state is the uniform
+ *             superposition; it is taken as H_B = sum_i (1 - sigma^x_i) / 2.
+ *   Sec. 4.3  H_P is diagonal: E(x) = number of clauses that assignment x leaves
+ *             unsatisfied (energy proportional to that count, constant 1).
+ *   Sec. 2.2  A K-SAT clause is a disjunction of literals x_i / NOT x_i.
+ * The state psi (2^n amplitudes, complex64 = interleaved float re, im) evolves by
+ * K second-order Strang steps of dt = T / K, step k frozen at s_k = (k + 1/2)/K:
+ *   exp(-i dt/2 s_k H_P) W exp(-i dt (1 - s_k) popcount) W exp(-i dt/2 s_k H_P),
+ * W the normalised Walsh-Hadamard transform (H_B = W diag(popcount) W).  The
+ * half phases of adjacent steps are merged, E(x) is recomputed from clause bit
+ * masks inside the kernels (bit exact), and the popcount phase is applied between
+ * two fused multi-qubit Walsh-Hadamard passes.
+ *
+ * Index convention (Sec. 2.1, basis |q_n ... q_1>): amplitude psi[x] belongs to
+ * the assignment with x_i = bit (i - 1) of x.
+ *
+ * Conventions for every entry point:
+ *   - Return a qaa_status; no C++ exception ever crosses this boundary.  On a
+ *     failure qaa_last_error() returns a message for the calling thread.
+ *   - Device pointers (psi, out_dev) are caller-owned CUDA device memory on the
+ *     current device; the library never frees or keeps them after the call.
+ *     psi must be 8-byte aligned and hold 2^n complex64 values.
+ *   - Work is enqueued on the handle's stream (qaa_set_stream; default: the
+ *     legacy default stream).  Calls that return a host value synchronise that
+ *     stream; the others are asynchronous with respect to the host.
+ *   - A handle is not thread safe: use one handle per host thread, or serialise.
+ */
+#ifndef QAA_H
+#define QAA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qaa_ctx* qaa_handle;
+
+typedef enum {
+  QAA_OK = 0,
+  QAA_PENDING = 1,      /* serving: the request has not finished yet            */
+  QAA_E_ARG = -1,       /* invalid argument (sizes, literals, null pointers)     */
+  QAA_E_NOMEM = -2,     /* device memory (or the configured budget) exhausted    */
+  QAA_E_CUDA = -3,      /* a CUDA runtime call failed; see qaa_last_error()      */
+  QAA_E_TIMEOUT = -4,   /* a bounded device wait gave up                         */
+  QAA_E_UNSAT = -5,     /* reserved: instance has no satisfying assignment       */
+  QAA_E_STATE = -6      /* call not valid in the object's current state          */
+} qaa_status;
+
+/* Largest number of qubits / variables accepted (2^34 complex64 = 128 GiB). */
+#define QAA_MAX_QUBITS 34
+/* Largest clause count accepted (energies must fit the 10-bit in-kernel counters). */
+#define QAA_MAX_CLAUSES 1023
+
+/* Library version, for the binding's sanity check. */
+int qaa_version(void);
+
+/* Thread-local message describing the last failure on this thread (never NULL). */
+const char* qaa_last_error(void);
+
+/*
+ * qaa_create -- build a handle for one K-SAT instance (Sec. 2.2) on the current
+ * CUDA device.
+ *   n        number of variables = qubits, 1 <= n <= QAA_MAX_QUBITS.
+ *   clauses  host array of m * 3 int32: clause c is clauses[3c .. 3c+2], each a
+ *            signed 1-based literal (+i = x_i, -i = NOT x_i) or 0 for an unused
+ *            slot (clauses of width 1..3).  Copied; the pointer is not kept.
+ *   m        number of clauses, 0 <= m <= QAA_MAX_CLAUSES (0 gives H_P = 0).
+ * Errors: QAA_E_ARG for n or m out of range, a literal with |lit| > n, a clause
+ * naming the same variable twice, or an all-zero clause; QAA_E_NOMEM/QAA_E_CUDA
+ * if the device tables cannot be allocated.  Repeated clauses are allowed and
+ * count with multiplicity in E(x).
+ */
+int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out);
+
+/* Release the handle and its device tables.  NULL is accepted. */
+int qaa_destroy(qaa_handle h);
+
+/* Bind a cudaStream_t (as void*) for all later work of this handle; NULL = default stream. */
+int qaa_set_stream(qaa_handle h, void* cuda_stream);
+
+/*
+ * qaa_set_variant -- choose the Walsh-Hadamard implementation.
+ *   wht_kind 0: FP32 CUDA-core butterflies (default).
+ *   q        reserved for the qubits-per-pass choice; 0 = automatic.
+ * Returns QAA_E_ARG for an unknown kind.
+ */
+int qaa_set_variant(qaa_handle h, int wht_kind, int q);
+
+/* psi[x] = 2^(-n/2) for all x: the ground state of H_B (Sec. 2.1).  Asynchronous. */
+int qaa_init_uniform(qaa_handle h, void* psi);
+
+/*
+ * qaa_evolve -- evolve psi in place from s = 0 to s = 1 over total time T with
+ * `steps` Strang steps (dt = T/steps), Eq. (1) with the linear sweep s = t/T.
+ * T >= 0, steps >= 1.  Asynchronous on the handle's stream.
+ */
+int qaa_evolve(qaa_handle h, void* psi, double T, int64_t steps);
+
+/*
+ * qaa_evolve_range -- only steps k0 <= k < k1 of the `steps`-step run of
+ * qaa_evolve (0 <= k0 <= k1 <= steps).  The half phases at both ends are
+ * applied unmerged, so running [0, j) then [j, K) reproduces [0, K) up to
+ * floating-point rounding: this is checkpoint / resume (psi plus k is the
+ * whole state of a run).  k0 == k1 is a no-op.
+ */
+int qaa_evolve_range(qaa_handle h, void* psi, double T, int64_t steps, int64_t k0, int64_t k1);
+
+/*
+ * qaa_evolve_schedule -- general schedule: `steps` Strang steps of length dt,
+ * step k frozen at s = s_values[k] (host array of `steps` doubles, each in any
+ * real range; 0..1 for the interpolation of Eq. (1)).  Used for non-linear
+ * sweeps and for frozen-s closed-form checks.
+ */
+int qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_values, int64_t steps);
+
+/*
+ * Observables, accumulated in FP64 from the complex64 state with a fixed
+ * two-level reduction order (bit-identical run to run).  Synchronous.
+ *   norm         sum_x |psi_x|^2
+ *   expect_hp    <H_P> = sum_x E(x) |psi_x|^2
+ *   expect_hb    <H_B> = n/2 norm - 1/2 sum_i Re sum_x conj(psi_x) psi_(x ^ 2^(i-1))
+ *   ground_prob  sum over E(x) = 0 of |psi_x|^2  (Sec. 2.1: ground manifold)
+ *   ground_count number of assignments with E(x) = 0 (the instance's solutions)
+ */
+typedef struct {
+  double norm;
+  double expect_hp;
+  double expect_hb;
+  double ground_prob;
+  int64_t ground_count;
+} qaa_obs;
+
+int qaa_observables(qaa_handle h, const void* psi, qaa_obs* out);
+
+/* <H(s)> = (1 - s) <H_B> + s <H_P> of Eq. (1), FP64, synchronous. */
+int qaa_energy(qaa_handle h, const void* psi, double s, double* out);
+
+/* Ground-state probability sum_{E(x)=0} |psi_x|^2, FP64, synchronous. */
+int qaa_success_prob(qaa_handle h, const void* psi, double* out);
+
+/* sum_x |psi_x|^2, FP64, synchronous. */
+int qaa_norm(qaa_handle h, const void* psi, double* out);
+
+/*
+ * qaa_hp_diagonal -- write E(x) for every x (2^n uint16 values, caller-owned
+ * device memory, 2-byte aligned) using the same in-kernel clause evaluation as
+ * the evolution.  Exposed for bit-exact checks.  Asynchronous.
+ */
+int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev);
+
+/*
+ * Launch profiling (tracing).  When enabled, the handle records a pair of CUDA
+ * events on its stream around every kernel it launches and accumulates, per
+ * kernel kind, the number of launches and their summed device time.
+ * qaa_profile_read synchronises the stream, folds in every pending pair and
+ * reports the totals since the last reset.  Event recording adds a few
+ * microseconds of stream work per launch.
+ */
+typedef enum {
+  QAA_K_LOW_FIRST = 0,     /* low pass: P then W over bits 0..9            */
+  QAA_K_LOW_MERGE = 1,     /* low pass: W, merged P, W                      */
+  QAA_K_LOW_LAST = 2,      /* low pass: W then P                            */
+  QAA_K_STRIDED = 3,       /* strided group pass: W                         */
+  QAA_K_STRIDED_PHASE = 4, /* top group pass: W, popcount phase, W          */
+  QAA_K_TABLES = 5,        /* FP64 phase-table generation                   */
+  QAA_K_ONCHIP = 6,        /* whole-run on-chip evolver (n <= 14)           */
+  QAA_K_OBSERVE = 7,       /* observable reductions (all kernels of a call) */
+  QAA_K_DIAG = 8,          /* E(x) export                                   */
+  QAA_K_INIT = 9,          /* uniform-state initialisation                  */
+  QAA_K_COUNT = 10
+} qaa_kernel_kind;
+
+int qaa_profile_enable(qaa_handle h, int on);
+int qaa_profile_reset(qaa_handle h);
+/* kind in [0, QAA_K_COUNT); launches and total_ms may be NULL.  Synchronous. */
+int qaa_profile_read(qaa_handle h, int kind, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAA_H */

@@ -1,0 +1,220 @@
+"""ctypes binding of libqaa.so (include/qaa.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  Device buffers are passed
+as raw pointers; ``torch`` tensors (complex64 for states, int16/uint16 for the
+energy diagonal) are accepted for convenience and only their ``data_ptr()`` is
+used.  If the shared library is missing this module raises ImportError: there
+is no fallback.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqaa.so")
+
+QAA_OK = 0
+QAA_PENDING = 1
+STATUS_NAMES = {0: "QAA_OK", 1: "QAA_PENDING", -1: "QAA_E_ARG", -2: "QAA_E_NOMEM", -3: "QAA_E_CUDA",
+                -4: "QAA_E_TIMEOUT", -5: "QAA_E_UNSAT", -6: "QAA_E_STATE"}
+MAX_QUBITS = 34
+MAX_CLAUSES = 1023
+
+
+class QaaError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_double), ("expect_hp", ctypes.c_double), ("expect_hb", ctypes.c_double),
+                ("ground_prob", ctypes.c_double), ("ground_count", ctypes.c_int64)]
+
+
+_c_int, _vp, _dbl, _i64 = ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_int64
+
+# name -> (restype, argtypes); the exported surface of include/qaa.h
+SIGNATURES = {
+    "qaa_version": (_c_int, []),
+    "qaa_last_error": (ctypes.c_char_p, []),
+    "qaa_create": (_c_int, [_c_int, _vp, _c_int, ctypes.POINTER(_vp)]),
+    "qaa_destroy": (_c_int, [_vp]),
+    "qaa_set_stream": (_c_int, [_vp, _vp]),
+    "qaa_set_variant": (_c_int, [_vp, _c_int, _c_int]),
+    "qaa_init_uniform": (_c_int, [_vp, _vp]),
+    "qaa_evolve": (_c_int, [_vp, _vp, _dbl, _i64]),
+    "qaa_evolve_range": (_c_int, [_vp, _vp, _dbl, _i64, _i64, _i64]),
+    "qaa_evolve_schedule": (_c_int, [_vp, _vp, _dbl, ctypes.POINTER(_dbl), _i64]),
+    "qaa_observables": (_c_int, [_vp, _vp, ctypes.POINTER(Obs)]),
+    "qaa_energy": (_c_int, [_vp, _vp, _dbl, ctypes.POINTER(_dbl)]),
+    "qaa_success_prob": (_c_int, [_vp, _vp, ctypes.POINTER(_dbl)]),
+    "qaa_norm": (_c_int, [_vp, _vp, ctypes.POINTER(_dbl)]),
+    "qaa_hp_diagonal": (_c_int, [_vp, _vp]),
+    "qaa_profile_enable": (_c_int, [_vp, _c_int]),
+    "qaa_profile_reset": (_c_int, [_vp]),
+    "qaa_profile_read": (_c_int, [_vp, _c_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
+}
+
+KERNEL_KINDS = ["low_first", "low_merge", "low_last", "strided", "strided_phase", "tables", "onchip",
+                "observe", "diag", "init"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1103_1399_gb300.build.build() "
+                          "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status):
+    if status != QAA_OK:
+        raise QaaError(status, lib.qaa_last_error().decode(errors="replace"))
+    return status
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("expected a device pointer (int) or an object with data_ptr()")
+
+
+def _check_state(inst, psi):
+    if hasattr(psi, "dtype"):
+        import torch
+        if psi.dtype != torch.complex64 or not psi.is_cuda or not psi.is_contiguous():
+            raise TypeError("psi must be a contiguous CUDA complex64 tensor")
+        if psi.numel() != (1 << inst.n):
+            raise ValueError(f"psi must have 2^{inst.n} elements")
+
+
+def flatten_clauses(clauses):
+    """List of clauses (each 1..3 signed literals) -> flat int32 buffer of m*3 (0-padded)."""
+    flat = []
+    for c in clauses:
+        c = [int(l) for l in c]
+        if not 1 <= len(c) <= 3:
+            raise ValueError("clauses must have 1..3 literals")
+        flat.extend(c + [0] * (3 - len(c)))
+    buf = (ctypes.c_int32 * max(len(flat), 1))(*flat) if flat else (ctypes.c_int32 * 1)(0)
+    return buf, len(clauses)
+
+
+class Instance:
+    """One 3-SAT instance on the current CUDA device (a qaa_handle)."""
+
+    def __init__(self, n, clauses, stream=None):
+        buf, m = flatten_clauses(clauses)
+        h = ctypes.c_void_p()
+        _check(lib.qaa_create(int(n), ctypes.cast(buf, ctypes.c_void_p), m, ctypes.byref(h)))
+        self._h = h
+        self.n = int(n)
+        self.m = m
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.qaa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        """stream: an int cudaStream_t, or a torch.cuda.Stream."""
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        _check(lib.qaa_set_stream(self._h, s))
+
+    def set_variant(self, wht_kind=0, q=0):
+        _check(lib.qaa_set_variant(self._h, int(wht_kind), int(q)))
+
+    def init_uniform(self, psi):
+        _check_state(self, psi)
+        _check(lib.qaa_init_uniform(self._h, _ptr(psi)))
+
+    def evolve(self, psi, T, steps):
+        _check_state(self, psi)
+        _check(lib.qaa_evolve(self._h, _ptr(psi), float(T), int(steps)))
+
+    def evolve_range(self, psi, T, steps, k0, k1):
+        _check_state(self, psi)
+        _check(lib.qaa_evolve_range(self._h, _ptr(psi), float(T), int(steps), int(k0), int(k1)))
+
+    def evolve_schedule(self, psi, dt, s_values):
+        _check_state(self, psi)
+        s = [float(v) for v in s_values]
+        arr = (ctypes.c_double * len(s))(*s)
+        _check(lib.qaa_evolve_schedule(self._h, _ptr(psi), float(dt), arr, len(s)))
+
+    def observables(self, psi):
+        _check_state(self, psi)
+        o = Obs()
+        _check(lib.qaa_observables(self._h, _ptr(psi), ctypes.byref(o)))
+        return {"norm": o.norm, "expect_hp": o.expect_hp, "expect_hb": o.expect_hb,
+                "ground_prob": o.ground_prob, "ground_count": int(o.ground_count)}
+
+    def energy(self, psi, s):
+        _check_state(self, psi)
+        out = ctypes.c_double()
+        _check(lib.qaa_energy(self._h, _ptr(psi), float(s), ctypes.byref(out)))
+        return out.value
+
+    def success_prob(self, psi):
+        _check_state(self, psi)
+        out = ctypes.c_double()
+        _check(lib.qaa_success_prob(self._h, _ptr(psi), ctypes.byref(out)))
+        return out.value
+
+    def norm(self, psi):
+        _check_state(self, psi)
+        out = ctypes.c_double()
+        _check(lib.qaa_norm(self._h, _ptr(psi), ctypes.byref(out)))
+        return out.value
+
+    def profile(self, on=True):
+        _check(lib.qaa_profile_enable(self._h, 1 if on else 0))
+
+    def profile_reset(self):
+        _check(lib.qaa_profile_reset(self._h))
+
+    def profile_read(self):
+        """{kind name: (launches, total_ms)} since the last reset (synchronises)."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            n = ctypes.c_int64()
+            ms = ctypes.c_double()
+            _check(lib.qaa_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)))
+            out[name] = (int(n.value), float(ms.value))
+        return out
+
+    def hp_diagonal(self, out):
+        """Write E(x) (uint16) for all x into a device buffer of 2^n 16-bit values."""
+        if hasattr(out, "numel") and out.numel() != (1 << self.n):
+            raise ValueError("out must have 2^n elements")
+        _check(lib.qaa_hp_diagonal(self._h, _ptr(out)))

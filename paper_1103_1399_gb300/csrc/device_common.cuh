@@ -1,0 +1,211 @@
+// Device helpers shared by the kernels: packed FP32 butterflies, complex
+// multiply, in-register Walsh-Hadamard stages, the per-tile clause fold and the
+// bit-sliced violated-clause counter.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qaa_internal.cuh"
+
+namespace qaa {
+
+// ---- packed FP32 arithmetic (sm_100+ f32x2) ---------------------------------
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+  return (static_cast<unsigned long long>(__float_as_uint(a.y)) << 32) | __float_as_uint(a.x);
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long u) {
+  return make_float2(__uint_as_float(static_cast<unsigned>(u)), __uint_as_float(static_cast<unsigned>(u >> 32)));
+}
+__device__ __forceinline__ void butterfly(float2& u, float2& w) {
+  unsigned long long a = f2_bits(u), b = f2_bits(w), s, d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s) : "l"(a), "l"(b));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  u = bits_f2(s);
+  w = bits_f2(d);
+}
+
+// a * z for complex a, z (FP32, fused multiply-add in both components).
+__device__ __forceinline__ float2 cmul(float2 a, float2 z) {
+  return make_float2(fmaf(a.x, z.x, -a.y * z.y), fmaf(a.x, z.y, a.y * z.x));
+}
+
+// Butterflies over register-index bits [B0, B1) of a 32-entry register tile:
+// for every bit b and every r with bit b clear, (v[r], v[r+2^b]) <- (v[r]+v[r+2^b], v[r]-v[r+2^b]).
+template <int B0, int B1>
+__device__ __forceinline__ void reg_wht(float2 (&v)[32]) {
+#pragma unroll
+  for (int b = B0; b < B1; ++b) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      if (!(r & (1 << b))) butterfly(v[r], v[r | (1 << b)]);
+    }
+  }
+}
+
+// Runtime-bounded variant (bits [b0, b1) with b0, b1 in [0, 5]).
+__device__ __forceinline__ void reg_wht_rt(float2 (&v)[32], int b0, int b1) {
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if (b >= b0 && b < b1) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        if (!(r & (1 << b))) butterfly(v[r], v[r | (1 << b)]);
+      }
+    }
+  }
+}
+
+// ---- clause fold for one 1024-amplitude tile (bits 0..9 vary) --------------
+// For tile index T = x >> 10 every clause either
+//   * has a literal on bits >= 10 that is true for the whole tile -> dropped,
+//   * has all its literals on bits >= 10 and all false -> +1 for every x (nconst),
+//   * otherwise stays active, reduced to its literals on bits 0..9.
+// Active clauses are written (warp-cooperatively, in clause order) to `act` as
+// {reg_pat, lane_pat}: the 32-bit truth tables over the register-held window and
+// over the lane-held window.  The list is padded with zero entries to a multiple
+// of 16 (a zero entry counts for nobody).
+template <bool REG_IS_LOW>
+__device__ __forceinline__ void fold_tile(const ClauseLP* __restrict__ s_cl, int m, unsigned tile_hi,
+                                          int lane, uint2* __restrict__ act, int& nconst, int& npad) {
+  int base = 0, cconst = 0;
+  for (int c0 = 0; c0 < m; c0 += 32) {
+    const int c = c0 + lane;
+    bool is_act = false, is_const = false;
+    uint2 e = make_uint2(0u, 0u);
+    if (c < m) {
+      const ClauseLP k = s_cl[c];
+      const bool hi_false = ((tile_hi ^ k.hi_viol) & k.hi_mask) == 0u;
+      const bool has_lo = (k.pat0 & k.pat5) != 0xffffffffu;
+      is_act = hi_false && has_lo;
+      is_const = hi_false && !has_lo;
+      e = REG_IS_LOW ? make_uint2(k.pat0, k.pat5) : make_uint2(k.pat5, k.pat0);
+    }
+    const unsigned ba = __ballot_sync(0xffffffffu, is_act);
+    const unsigned bc = __ballot_sync(0xffffffffu, is_const);
+    if (is_act) act[base + __popc(ba & ((1u << lane) - 1u))] = e;
+    base += __popc(ba);
+    cconst += __popc(bc);
+  }
+  const int padded = (base + 15) & ~15;
+  if (lane < padded - base) act[base + lane] = make_uint2(0u, 0u);
+  __syncwarp();
+  nconst = cconst;
+  npad = padded;
+}
+
+// ---- bit-sliced counting ----------------------------------------------------
+// Carry-save adder: (h, l) <- carry and sum of l + b + c (all bit-parallel).
+__device__ __forceinline__ void csa(unsigned& h, unsigned& l, unsigned b, unsigned c) {
+  const unsigned a = l;
+  l = a ^ b ^ c;
+  h = (a & b) | (a & c) | (b & c);
+}
+
+// For every register index r (0..31) count the active entries whose lane_pat
+// has `lanebit` set and whose reg_pat has bit r set.  Result: pl[b] holds bit b
+// of each of the 32 counts (bit r of pl[b] belongs to register r).  Harley-Seal
+// carry-save tree over 16 entries at a time, then a ripple add of the weight-16
+// carries.  Counts up to 1023 are exact.
+__device__ __forceinline__ void count_active(const uint2* __restrict__ act, int npad, unsigned lanebit,
+                                             unsigned (&pl)[kPlanes]) {
+  unsigned ones = 0, twos = 0, fours = 0, eights = 0;
+  unsigned hi[kPlanes - 4];
+#pragma unroll
+  for (int k = 0; k < kPlanes - 4; ++k) hi[k] = 0;
+  for (int i = 0; i < npad; i += 16) {
+    unsigned d[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint2 e = act[i + j];
+      d[j] = (e.y & lanebit) ? e.x : 0u;
+    }
+    unsigned twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
+    csa(twosA, ones, d[0], d[1]);
+    csa(twosB, ones, d[2], d[3]);
+    csa(foursA, twos, twosA, twosB);
+    csa(twosA, ones, d[4], d[5]);
+    csa(twosB, ones, d[6], d[7]);
+    csa(foursB, twos, twosA, twosB);
+    csa(eightsA, fours, foursA, foursB);
+    csa(twosA, ones, d[8], d[9]);
+    csa(twosB, ones, d[10], d[11]);
+    csa(foursA, twos, twosA, twosB);
+    csa(twosA, ones, d[12], d[13]);
+    csa(twosB, ones, d[14], d[15]);
+    csa(foursB, twos, twosA, twosB);
+    csa(eightsB, fours, foursA, foursB);
+    csa(sixteens, eights, eightsA, eightsB);
+    unsigned carry = sixteens;
+#pragma unroll
+    for (int k = 0; k < kPlanes - 4; ++k) {
+      const unsigned t = hi[k] & carry;
+      hi[k] ^= carry;
+      carry = t;
+    }
+  }
+  pl[0] = ones;
+  pl[1] = twos;
+  pl[2] = fours;
+  pl[3] = eights;
+#pragma unroll
+  for (int k = 0; k < kPlanes - 4; ++k) pl[4 + k] = hi[k];
+}
+
+// Counts of registers R and R+16 packed as (count_R) | (count_{R+16} << 16).
+template <int R>
+__device__ __forceinline__ unsigned extract_pair(const unsigned (&pl)[kPlanes]) {
+  unsigned w = 0;
+#pragma unroll
+  for (int b = 0; b < kPlanes; ++b) {
+    const unsigned s = (R >= b) ? (pl[b] >> (R - b)) : (pl[b] << (b - R));
+    w |= s & (0x00010001u << b);
+  }
+  return w;
+}
+
+template <int R>
+struct ApplyPhaseUnroll {
+  __device__ __forceinline__ static void run(float2 (&v)[32], const unsigned (&pl)[kPlanes], int nconst,
+                                             const float2* __restrict__ tab) {
+    const unsigned w = extract_pair<R>(pl);
+    v[R] = cmul(v[R], tab[nconst + static_cast<int>(w & 0xffffu)]);
+    v[R + 16] = cmul(v[R + 16], tab[nconst + static_cast<int>(w >> 16)]);
+    ApplyPhaseUnroll<R + 1>::run(v, pl, nconst, tab);
+  }
+};
+template <>
+struct ApplyPhaseUnroll<16> {
+  __device__ __forceinline__ static void run(float2 (&)[32], const unsigned (&)[kPlanes], int, const float2*) {}
+};
+
+// v[r] <- exp(-i theta E(x_r)) v[r] where E = nconst + the bit-sliced count in
+// pl and tab[E] holds the FP32-rounded FP64 phase (the P row of the step).
+__device__ __forceinline__ void apply_p_phase(float2 (&v)[32], const unsigned (&pl)[kPlanes], int nconst,
+                                              const float2* __restrict__ tab) {
+  ApplyPhaseUnroll<0>::run(v, pl, nconst, tab);
+}
+
+template <int R>
+struct StoreCountUnroll {
+  __device__ __forceinline__ static void run(int (&e)[32], const unsigned (&pl)[kPlanes], int nconst) {
+    const unsigned w = extract_pair<R>(pl);
+    e[R] = nconst + static_cast<int>(w & 0xffffu);
+    e[R + 16] = nconst + static_cast<int>(w >> 16);
+    StoreCountUnroll<R + 1>::run(e, pl, nconst);
+  }
+};
+template <>
+struct StoreCountUnroll<16> {
+  __device__ __forceinline__ static void run(int (&)[32], const unsigned (&)[kPlanes], int) {}
+};
+
+// E(x_r) for the 32 register-held amplitudes.
+__device__ __forceinline__ void energies(int (&e)[32], const uint2* __restrict__ act, int npad, int nconst,
+                                         unsigned lanebit) {
+  unsigned pl[kPlanes];
+  count_active(act, npad, lanebit, pl);
+  StoreCountUnroll<0>::run(e, pl, nconst);
+}
+
+}  // namespace qaa

@@ -1,0 +1,88 @@
+// Internal declarations shared by the kernels and the host engine.
+//
+// Data layout in HBM: the state is one caller-owned array of 2^n complex64
+// (float2, re/im interleaved), psi[x] for the assignment x (x_i = bit i-1).
+// Clause tables live in device memory owned by the handle:
+//   ClauseMV  : {mask, viol} 64-bit pair; clause c is violated by x iff
+//               (x & mask) == viol  (mask = its variables, viol = the value of
+//               each that makes the literal false).  Sec. 2.2 / Sec. 4.3.
+//   ClauseLP  : the same clause split for a 1024-amplitude tile (bits 0..9):
+//               hi_mask/hi_viol over bits >= 10 (shifted down by 10), and two
+//               32-bit truth tables pat0 / pat5: bit j of pat0 is set iff the
+//               clause's literals on bits 0..4 are all false when those bits
+//               equal j (all ones if the clause has none there); pat5 likewise
+//               for bits 5..9.  Violated(x) = hi part false AND pat0 bit
+//               (x & 31) AND pat5 bit ((x >> 5) & 31).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qaa {
+
+struct __align__(16) ClauseMV {
+  unsigned long long mask;
+  unsigned long long viol;
+};
+
+struct __align__(16) ClauseLP {
+  unsigned hi_mask;
+  unsigned hi_viol;
+  unsigned pat0;
+  unsigned pat5;
+};
+
+// Low-pass tile: bits 0..9 of the index, 1024 amplitudes, one warp.
+constexpr int kLowBits = 10;
+constexpr int kLowTile = 1 << kLowBits;
+
+// In-register bit-sliced counters hold up to 10 bits (QAA_MAX_CLAUSES = 1023).
+constexpr int kPlanes = 10;
+
+// ---- pass descriptors -------------------------------------------------------
+enum PassKind : int {
+  kLpFirst = 0,  // psi <- W_G1 P(row) psi                 (first pass of a range)
+  kLpMerge = 1,  // psi <- W_G1 P(row) W_G1 psi            (step boundary, merged)
+  kLpLast = 2,   // psi <- P(row) W_G1 psi                 (last pass of a range)
+  kSpW = 3,      // psi <- W_G psi over a strided group G
+  kSpWBW = 4,    // psi <- W_G B(row) W_G psi over the top group
+  kLpAll = 5,    // n <= 10: psi <- P W B W P for one step (single tile)
+};
+
+struct Pass {
+  int kind;
+  int a;      // first bit of the active group (strided passes)
+  int q;      // active bits (strided passes)
+  int prow;   // phase-table row for P (low passes)
+  int prow2;  // second P row (kLpAll)
+  int brow;   // popcount-phase row (kSpWBW / kLpAll)
+};
+
+// ---- kernel launchers (defined in the .cu files) ----------------------------
+struct LaunchCtx {
+  cudaStream_t stream;
+  int num_sms;
+};
+
+cudaError_t launch_init_uniform(const LaunchCtx& lc, float2* psi, int n);
+// Phase tables for steps c0 <= k < c1 of the range [k0, k1) of a K-step run:
+// c1-c0+1 P rows of m+1 entries and c1-c0 B rows of n+1 entries.
+cudaError_t launch_tables(const LaunchCtx& lc, float2* ptab, float2* btab, int n, int m, double dt,
+                          const double* s_dev, long long K, long long k0, long long k1, long long c0, long long c1);
+cudaError_t launch_pass(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m,
+                        const ClauseLP* cl, const float2* ptab, const float2* btab);
+// n <= kOnchipMaxBits: the whole state stays in one CTA's shared memory for
+// `nsteps` steps.  P row j (j = 0..nsteps) and B row j (j < nsteps) as produced
+// by launch_tables; first_p = apply P row 0 before the first transform.
+constexpr int kOnchipMaxBits = 14;
+cudaError_t launch_onchip(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseMV* cl,
+                          const float2* ptab, const float2* btab, int nsteps, bool first_p);
+size_t onchip_smem_bytes(int n, int m);
+cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, const ClauseLP* cl);
+// Observables: partials has room for obs_partials_len(n) doubles; result is 5 doubles
+// {norm, <H_P>, ground_prob, ground_count, sum of pair correlations} on the device.
+size_t obs_partials_len(int n, int num_sms);
+cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, int m,
+                               const ClauseLP* cl, double* partials, double* result);
+
+}  // namespace qaa
