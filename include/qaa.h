@@ -156,6 +156,38 @@ int qaa_norm(qaa_handle h, const void* psi, double* out);
 int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev);
 
 /*
+ * qaa_observables_noalloc -- the same five observables as qaa_observables,
+ * for callers that cannot allocate device memory.  A library addition: the
+ * paper has no counterpart.
+ *
+ * Some callers cannot call cudaMalloc: their device memory belongs to another
+ * allocator (a host framework's memory pool, a budget fixed at start-up), or
+ * they run latency-critical loops in which cudaMalloc / cudaFree are not
+ * acceptable because those calls can synchronise the whole device.  Such a
+ * caller cannot create a qaa_handle (qaa_create allocates its clause tables),
+ * so this entry point takes the instance directly and allocates nothing:
+ *   n, clauses, m  the instance, exactly as for qaa_create (host array);
+ *   psi            the caller's device state (2^n complex64, 8-byte aligned);
+ *   cuda_stream    stream to run on (NULL = default stream); synchronised
+ *                  before returning;
+ *   out            host result.
+ * Its scratch (encoded clause table, per-block partial sums, results) is one
+ * static device array of about 80 KiB that every GPU which loads this library
+ * holds until the process exits.  Limits: m <= QAA_MAX_CLAUSES, and the
+ * partial sums a call needs, (5 + ceil((n - 10) / 5)) x 2 x (SM count) for
+ * n > 10, must not exceed QAA_NOALLOC_MAX_PARTIALS; larger requests return
+ * QAA_E_ARG with a message in qaa_last_error().
+ * The first call made on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * whose work can overlap on the GPU (from several threads or streams) race and
+ * must be serialised by the caller.
+ */
+#define QAA_NOALLOC_MAX_PARTIALS 8192
+int qaa_observables_noalloc(int n, const int32_t* clauses, int m, const void* psi, void* cuda_stream,
+                            qaa_obs* out);
+
+/*
  * Launch profiling (tracing).  When enabled, the handle records a pair of CUDA
  * events on its stream around every kernel it launches and accumulates, per
  * kernel kind, the number of launches and their summed device time.

@@ -51,6 +51,7 @@ SIGNATURES = {
     "qaa_success_prob": (_c_int, [_vp, _vp, ctypes.POINTER(_dbl)]),
     "qaa_norm": (_c_int, [_vp, _vp, ctypes.POINTER(_dbl)]),
     "qaa_hp_diagonal": (_c_int, [_vp, _vp]),
+    "qaa_observables_noalloc": (_c_int, [_c_int, _vp, _c_int, _vp, _vp, ctypes.POINTER(Obs)]),
     "qaa_profile_enable": (_c_int, [_vp, _c_int]),
     "qaa_profile_reset": (_c_int, [_vp]),
     "qaa_profile_read": (_c_int, [_vp, _c_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),

@@ -311,6 +311,10 @@ int observe(qaa_ctx* h, const void* psi, double out[5]) {
 
 }  // namespace
 
+namespace qaa {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace qaa
+
 extern "C" {
 
 int qaa_version(void) { return 1; }

@@ -16,6 +16,8 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace qaa {
@@ -84,5 +86,8 @@ cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, con
 size_t obs_partials_len(int n, int num_sms);
 cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, int m,
                                const ClauseLP* cl, double* partials, double* result);
+
+// Store a message for qaa_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 }  // namespace qaa
