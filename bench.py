@@ -39,12 +39,18 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # for the dominant kernel, with the sha256 of the kernel sources at the time of
 # the capture; a mismatch (kernel changed since) reports traffic = null.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu full-set capture of sp_tma_kernel<10,4,false> on the n=28 instance with
+    # QAA_GROUP_BITS=10,8 (profiles/sp_tma_kernel_q10_run128_plain_n28.md):
+    # 2.14779e9 + 2.08700e9 bytes per launch for 2^28 amplitudes, scaled by the
+    # amplitude count (x4) to one n=30 launch.
+    "strided": {"bytes_per_launch": 4 * (2.147790e9 + 2.086998e9), "src_sha": "97b1a36261a39f1f"},
+}
 
 
 def kernel_src_sha():
     h = hashlib.sha256()
-    for f in ("device_common.cuh", "pass_kernels.cu", "qaa_internal.cuh"):
+    for f in ("device_common.cuh", "tma_kernels.cu", "qaa_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1103_1399_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -199,7 +205,7 @@ def run_ours(args):
     import satgen
     import paper_1103_1399_gb300 as q
 
-    inst_d = satgen.load_instance(INSTANCE)
+    inst_d = satgen.load_instance(args.instance)
     n, clauses = inst_d["n"], inst_d["clauses"]
     stream = torch.cuda.current_stream()
     psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
@@ -238,7 +244,7 @@ def run_ours(args):
     obs = inst.observables(psi)
 
     state_bytes = 8 * (1 << n)
-    passes_per_step = 4
+    passes_per_step = round(sum(prof[k][0] for k in ("low_first", "low_merge", "low_last", "strided", "strided_phase")) / K)
     hbm_gbs = passes_per_step * 2 * state_bytes * K / (ms / 1e3) / 1e9
 
     # dominant kernel, its average launch, roofline
@@ -285,9 +291,9 @@ def run_ours(args):
             "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"planted 3-SAT n={n} m={len(clauses)}, linear s, dt={DT} "
-                                   f"(T={T_CONFIG:g} / 400-step configuration), complex64 state 8 GiB",
-                       "n": n, "m": len(clauses), "dt": DT, "plan": "low pass bits 0-9 + strided 10-19, 20-29; "
-                       "4 HBM round trips per step", "l2": "state (8 GiB) exceeds L2; no flush needed",
+                                   f"(T={T_CONFIG:g} / 400-step configuration), complex64 state {state_bytes / 2**30:g} GiB",
+                       "n": n, "m": len(clauses), "dt": DT, "plan": inst.describe_plan(),
+                       "l2": f"state ({state_bytes / 2**30:g} GiB) exceeds L2; no flush needed",
                        "parallelism": f"replicas x{ws}"},
             "hbm_gbs": hbm_gbs,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -302,6 +308,7 @@ def run_ours(args):
             "final": {"norm": obs["norm"], "ground_prob": obs["ground_prob"]},
         }
         print(json.dumps(line))
+    inst.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -315,6 +322,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--instance", default=INSTANCE,
+                    help="committed instance to evolve (default: the n=30 benchmark instance); smaller ones are "
+                         "for profiling captures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -24,7 +24,9 @@
  *     failure qaa_last_error() returns a message for the calling thread.
  *   - Device pointers (psi, out_dev) are caller-owned CUDA device memory on the
  *     current device; the library never frees or keeps them after the call.
- *     psi must be 8-byte aligned and hold 2^n complex64 values.
+ *     psi must hold 2^n complex64 values; the evolution calls need it 16-byte
+ *     aligned (as every cudaMalloc / PyTorch allocation is), the read-only
+ *     calls 8-byte aligned.
  *   - Work is enqueued on the handle's stream (qaa_set_stream; default: the
  *     legacy default stream).  Calls that return a host value synchronise that
  *     stream; the others are asynchronous with respect to the host.
@@ -154,6 +156,15 @@ int qaa_norm(qaa_handle h, const void* psi, double* out);
  * the evolution.  Exposed for bit-exact checks.  Asynchronous.
  */
 int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev);
+
+/*
+ * qaa_describe_plan -- write a one-line, NUL-terminated description of how this
+ * handle evolves a state (on-chip, or the streaming pass plan: groups of index
+ * bits, run lengths, passes per step, load path) into buf (len bytes,
+ * truncated to fit).  Host only; no CUDA work.  A library addition: the paper
+ * has no counterpart.
+ */
+int qaa_describe_plan(qaa_handle h, char* buf, size_t len);
 
 /*
  * qaa_observables_noalloc -- the same five observables as qaa_observables,

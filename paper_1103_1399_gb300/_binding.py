@@ -52,6 +52,7 @@ SIGNATURES = {
     "qaa_norm": (_c_int, [_vp, _vp, ctypes.POINTER(_dbl)]),
     "qaa_hp_diagonal": (_c_int, [_vp, _vp]),
     "qaa_observables_noalloc": (_c_int, [_c_int, _vp, _c_int, _vp, _vp, ctypes.POINTER(Obs)]),
+    "qaa_describe_plan": (_c_int, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
     "qaa_profile_enable": (_c_int, [_vp, _c_int]),
     "qaa_profile_reset": (_c_int, [_vp]),
     "qaa_profile_read": (_c_int, [_vp, _c_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
@@ -197,6 +198,11 @@ class Instance:
         out = ctypes.c_double()
         _check(lib.qaa_norm(self._h, _ptr(psi), ctypes.byref(out)))
         return out.value
+
+    def describe_plan(self):
+        buf = ctypes.create_string_buffer(512)
+        _check(lib.qaa_describe_plan(self._h, buf, 512))
+        return buf.value.decode()
 
     def profile(self, on=True):
         _check(lib.qaa_profile_enable(self._h, 1 if on else 0))

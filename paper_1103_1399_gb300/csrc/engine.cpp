@@ -13,6 +13,7 @@
 // 2g-2 HBM round trips for g groups.  n <= 14 runs entirely on chip.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -41,7 +42,7 @@ int fail(int code, const std::string& msg) {
 constexpr long long kChunkSteps = 1024;
 
 struct Group {
-  int a, q;
+  int a, q, a2;  // active bits [a, a+5) and [a2, a2+q-5); a2 == a + 5 for a contiguous group
 };
 
 }  // namespace
@@ -62,6 +63,11 @@ struct qaa_ctx {
   size_t part_cap = 0;
   double* d_res = nullptr;
   double* h_res = nullptr;  // pinned
+  int* d_err = nullptr;     // set by kernels whose bounded waits expired
+  bool use_tma = true;      // TMA-pipelined streaming passes (QAA_PASSES=classic selects the others)
+  int phase_group = 1 << 20;  // strided group hosting the popcount phase (default: the top one)
+  bool split_groups = true;   // recombine two 10-bit strided groups (see plan_groups)
+  int run128_groups = -1;     // bit i set: strided group i uses 128-byte runs (-1: default policy)
   std::vector<Group> strided;  // ascending bit order; back() is the top group
   // launch profiling
   bool prof = false;
@@ -113,17 +119,45 @@ int encode(qaa_ctx* h, const int32_t* clauses) {
   return QAA_OK;
 }
 
+// Strided groups above the low pass: the n-10 remaining bits in groups of 5..10
+// (as equal as possible), or the sizes given in QAA_GROUP_BITS ("10,8"), a
+// tuning override.
 void plan_groups(qaa_ctx* h) {
   h->strided.clear();
   if (h->n <= qaa::kOnchipMaxBits) return;
   const int rest = h->n - qaa::kLowBits;
-  const int ng = (rest + 9) / 10;
-  const int base = rest / ng, extra = rest % ng;
+  std::vector<int> sizes;
+  if (const char* gb = std::getenv("QAA_GROUP_BITS")) {
+    int sum = 0;
+    bool ok = true;
+    for (const char* p = gb; *p;) {
+      const int q = std::atoi(p);
+      if (q < 5 || q > 10) ok = false;
+      sizes.push_back(q);
+      sum += q;
+      while (*p && *p != ',') ++p;
+      if (*p == ',') ++p;
+    }
+    if (!ok || sum != rest) sizes.clear();
+  }
+  if (sizes.empty()) {
+    const int ng = (rest + 9) / 10;
+    const int base = rest / ng, extra = rest % ng;
+    for (int g = 0; g < ng; ++g) sizes.push_back(base + (g < extra ? 1 : 0));
+  }
   int a = qaa::kLowBits;
-  for (int g = 0; g < ng; ++g) {
-    const int q = base + (g < extra ? 1 : 0);
-    h->strided.push_back({a, q});
+  for (int q : sizes) {
+    h->strided.push_back({a, q, a + 5});
     a += q;
+  }
+  // Two 10-bit strided groups [10,20) and [20,30): recombine them as
+  // {10..14, 25..29} and {15..24}.  With [20,30) as one group every tile has
+  // 1024 rows 8 MiB apart, each on its own memory page; recombined, a tile
+  // spans at most 128 pages.
+  if (h->split_groups && h->strided.size() == 2 && h->strided[0].q == 10 && h->strided[1].q == 10) {
+    const int b = qaa::kLowBits;
+    h->strided[0] = {b, 10, b + 15};
+    h->strided[1] = {b + 5, 10, b + 10};
   }
 }
 
@@ -194,28 +228,41 @@ int ensure_tab(qaa_ctx* h, size_t entries) {
   return QAA_OK;
 }
 
+// The popcount phase B needs every qubit in the Hadamard basis, so it is applied
+// inside the pass of whichever strided group is transformed last (the "phase
+// group"); the others are transformed before it (in ascending order) and after
+// it (descending).
 void build_passes(const qaa_ctx* h, long long k0, long long k1, long long c0, long long c1,
                   std::vector<qaa::Pass>& out) {
   out.clear();
-  const Group top = h->strided.back();
-  const int nmid = static_cast<int>(h->strided.size()) - 1;
+  const int ng = static_cast<int>(h->strided.size());
+  const int pg = h->phase_group < ng ? h->phase_group : ng - 1;
+  const Group top = h->strided[pg];
+  // Contiguous run per tile row: 128 bytes for the plain strided passes, 64
+  // bytes (more CTAs per SM) for the heavier pass that hosts the phase.
+  auto runc = [&](int i) {
+    if (h->run128_groups >= 0) return ((h->run128_groups >> i) & 1) ? 4 : 0;
+    return i == pg ? 0 : 4;
+  };
   auto mid_up = [&]() {
-    for (int i = 0; i < nmid; ++i) out.push_back({qaa::kSpW, h->strided[i].a, h->strided[i].q, 0, 0, 0});
+    for (int i = 0; i < ng; ++i)
+      if (i != pg) out.push_back({qaa::kSpW, h->strided[i].a, h->strided[i].q, 0, runc(i), 0, h->strided[i].a2});
   };
   auto mid_down = [&]() {
-    for (int i = nmid - 1; i >= 0; --i) out.push_back({qaa::kSpW, h->strided[i].a, h->strided[i].q, 0, 0, 0});
+    for (int i = ng - 1; i >= 0; --i)
+      if (i != pg) out.push_back({qaa::kSpW, h->strided[i].a, h->strided[i].q, 0, runc(i), 0, h->strided[i].a2});
   };
   if (c0 == k0) {
-    out.push_back({qaa::kLpFirst, 0, 0, 0, 0, 0});
+    out.push_back({qaa::kLpFirst, 0, 0, 0, 0, 0, 0});
     mid_up();
   }
   for (long long k = c0; k < c1; ++k) {
-    out.push_back({qaa::kSpWBW, top.a, top.q, 0, 0, static_cast<int>(k - c0)});
+    out.push_back({qaa::kSpWBW, top.a, top.q, 0, runc(pg), static_cast<int>(k - c0), top.a2});
     mid_down();
     if (k == k1 - 1) {
-      out.push_back({qaa::kLpLast, 0, 0, static_cast<int>(k + 1 - c0), 0, 0});
+      out.push_back({qaa::kLpLast, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0});
     } else {
-      out.push_back({qaa::kLpMerge, 0, 0, static_cast<int>(k + 1 - c0), 0, 0});
+      out.push_back({qaa::kLpMerge, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0});
       mid_up();
     }
   }
@@ -227,11 +274,22 @@ int check_handle(qaa_ctx* h) {
   return QAA_OK;
 }
 
+// After a stream synchronisation: report (and clear) an expired device wait.
+int check_device_error(qaa_ctx* h) {
+  int e = 0;
+  QAA_CK(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    QAA_CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    return fail(QAA_E_TIMEOUT, "a bounded wait on a TMA copy expired in a streaming pass");
+  }
+  return QAA_OK;
+}
+
 int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, long long k1, const double* s_host) {
   int st = check_handle(h);
   if (st) return st;
   if (!psi) return fail(QAA_E_ARG, "psi is null");
-  if (reinterpret_cast<uintptr_t>(psi) % 8u) return fail(QAA_E_ARG, "psi must be 8-byte aligned");
+  if (reinterpret_cast<uintptr_t>(psi) % 16u) return fail(QAA_E_ARG, "psi must be 16-byte aligned");
   if (K < 1 || k0 < 0 || k1 < k0 || k1 > K) return fail(QAA_E_ARG, "bad step range");
   if (!std::isfinite(dt)) return fail(QAA_E_ARG, "dt must be finite");
   if (k0 == k1) return QAA_OK;
@@ -274,8 +332,12 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
       }));
     } else {
       build_passes(h, k0, k1, c0, c1, passes);
+      const bool tma = h->use_tma;
       for (const qaa::Pass& ps : passes)
-        QAA_CK(timed(h, ps.kind, [&] { return qaa::launch_pass(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab); }));
+        QAA_CK(timed(h, ps.kind, [&] {
+          return tma ? qaa::launch_pass_tma(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab, h->d_err)
+                     : qaa::launch_pass(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab);
+        }));
     }
   }
   return QAA_OK;
@@ -306,7 +368,7 @@ int observe(qaa_ctx* h, const void* psi, double out[5]) {
   QAA_CK(cudaMemcpyAsync(h->h_res, h->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   QAA_CK(cudaStreamSynchronize(h->stream));
   std::memcpy(out, h->h_res, 5 * sizeof(double));
-  return QAA_OK;
+  return check_device_error(h);
 }
 
 }  // namespace
@@ -336,7 +398,6 @@ int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out) {
     delete h;
     return st;
   }
-  plan_groups(h);
   auto cleanup = [&](int code, const std::string& msg) {
     qaa_destroy(h);
     return fail(code, msg);
@@ -348,9 +409,22 @@ int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out) {
   if (cudaMalloc(&h->d_mv, mcap * sizeof(qaa::ClauseMV)) != cudaSuccess ||
       cudaMalloc(&h->d_lp, mcap * sizeof(qaa::ClauseLP)) != cudaSuccess ||
       cudaMalloc(&h->d_res, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&h->h_res, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(QAA_E_NOMEM, "cannot allocate clause tables");
+  }
+  if (cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess) return cleanup(QAA_E_CUDA, "cannot clear error word");
+  {
+    const char* env = std::getenv("QAA_PASSES");
+    h->use_tma = qaa::tma_available() && !(env && std::strcmp(env, "classic") == 0);
+    const char* pg = std::getenv("QAA_PHASE_GROUP");
+    if (pg) h->phase_group = std::atoi(pg);
+    const char* rg = std::getenv("QAA_RUN128_GROUPS");
+    if (rg) h->run128_groups = std::atoi(rg);
+    const char* sg = std::getenv("QAA_SPLIT_GROUPS");
+    h->split_groups = h->use_tma && !(sg && std::atoi(sg) == 0);
+    plan_groups(h);
   }
   if (m > 0) {
     if (cudaMemcpy(h->d_mv, h->mv.data(), m * sizeof(qaa::ClauseMV), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -371,6 +445,7 @@ int qaa_destroy(qaa_handle h) {
   cudaFree(h->d_s);
   cudaFree(h->d_part);
   cudaFree(h->d_res);
+  cudaFree(h->d_err);
   if (h->h_res) cudaFreeHost(h->h_res);
   for (auto& p : h->pending) {
     cudaEventDestroy(p.a);
@@ -472,6 +547,32 @@ int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev) {
   return QAA_OK;
 }
 
+int qaa_describe_plan(qaa_handle h, char* buf, size_t len) {
+  if (!h) return fail(QAA_E_ARG, "null handle");
+  if (!buf || len == 0) return fail(QAA_E_ARG, "buf is null or empty");
+  std::string d;
+  if (h->n <= qaa::kOnchipMaxBits) {
+    d = "on-chip: whole run in one CTA's shared memory (n=" + std::to_string(h->n) + ")";
+  } else {
+    const int ng = static_cast<int>(h->strided.size());
+    const int pg = h->phase_group < ng ? h->phase_group : ng - 1;
+    d = "streaming, " + std::string(h->use_tma ? "TMA" : "classic") + " loads; low pass bits [0,10) W.P.W";
+    for (int i = 0; i < ng; ++i) {
+      const Group& g = h->strided[i];
+      int c = i == pg ? 0 : 4;
+      if (h->run128_groups >= 0) c = ((h->run128_groups >> i) & 1) ? 4 : 0;
+      d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";
+      if (g.q > 5) d += "+[" + std::to_string(g.a2) + "," + std::to_string(g.a2 + g.q - 5) + ")";
+      d += i == pg ? " W.B.W" : " W";
+      if (h->use_tma) d += c == 4 ? " 128B runs" : " 64B runs";
+    }
+    d += "; " + std::to_string(2 * (ng + 1) - 2) + " HBM round trips per step";
+  }
+  std::strncpy(buf, d.c_str(), len - 1);
+  buf[len - 1] = '\0';
+  return QAA_OK;
+}
+
 int qaa_profile_enable(qaa_handle h, int on) {
   int st = check_handle(h);
   if (st) return st;
@@ -500,6 +601,9 @@ int qaa_profile_read(qaa_handle h, int kind, int64_t* launches, double* total_ms
   if (st) return st;
   if (kind < 0 || kind >= QAA_K_COUNT) return fail(QAA_E_ARG, "unknown kernel kind");
   st = fold_profile(h);
+  if (st) return st;
+  QAA_CK(cudaStreamSynchronize(h->stream));
+  st = check_device_error(h);
   if (st) return st;
   if (launches) *launches = h->prof_n[kind];
   if (total_ms) *total_ms = h->prof_ms[kind];

@@ -47,17 +47,17 @@ enum PassKind : int {
   kLpMerge = 1,  // psi <- W_G1 P(row) W_G1 psi            (step boundary, merged)
   kLpLast = 2,   // psi <- P(row) W_G1 psi                 (last pass of a range)
   kSpW = 3,      // psi <- W_G psi over a strided group G
-  kSpWBW = 4,    // psi <- W_G B(row) W_G psi over the top group
-  kLpAll = 5,    // n <= 10: psi <- P W B W P for one step (single tile)
+  kSpWBW = 4,    // psi <- W_G B(row) W_G psi over the phase group
 };
 
 struct Pass {
   int kind;
-  int a;      // first bit of the active group (strided passes)
+  int a;      // strided passes: index bit of the group's lowest 5 active bits
   int q;      // active bits (strided passes)
   int prow;   // phase-table row for P (low passes)
-  int prow2;  // second P row (kLpAll)
-  int brow;   // popcount-phase row (kSpWBW / kLpAll)
+  int run_c;  // strided passes: 4 = 128-byte contiguous runs per tile row, 0 = default
+  int brow;   // popcount-phase row (kSpWBW)
+  int a2;     // strided passes: index bit of active bits 5..q-1 (a + 5 for a contiguous group)
 };
 
 // ---- kernel launchers (defined in the .cu files) ----------------------------
@@ -86,6 +86,13 @@ cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, con
 size_t obs_partials_len(int n, int num_sms);
 cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, int m,
                                const ClauseLP* cl, double* partials, double* result);
+
+// TMA-pipelined variants of the streaming passes (tma_kernels.cu).  err is a
+// device word set to nonzero when a bounded wait expires.  psi must be 16-byte
+// aligned.
+bool tma_available();
+cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
+                            const float2* ptab, const float2* btab, int* err);
 
 // Store a message for qaa_last_error() on the calling thread.
 void set_last_error(const std::string& msg);

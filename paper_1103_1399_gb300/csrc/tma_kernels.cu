@@ -1,0 +1,455 @@
+// TMA-pipelined streaming passes (n >= 15).  Same arithmetic as the passes in
+// pass_kernels.cu; what changes is how the state moves between HBM and the SM.
+//
+// * Strided passes (W over a group of Q index bits, or W B W over the top
+//   group): persistent CTAs, two dense 2^(Q+C)-amplitude tile buffers filled by
+//   4-D cp.async.bulk.tensor loads that complete on an mbarrier.  While a tile
+//   is transformed in registers, the TMA engine already fetches the tile after
+//   next into the other buffer.  Results go straight from registers to HBM.
+// * Low passes (W P W over bits 0..9): every warp owns two 8 KiB buffers filled
+//   by 1-D cp.async.bulk copies; the clause fold and bit-sliced count for a tile
+//   run while its data is still in flight.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel records an error
+// word that the host reports as QAA_E_TIMEOUT, and all threads of the block (or
+// lanes of the warp) leave together.
+#include <cuda.h>
+
+#include "device_common.cuh"
+
+namespace qaa {
+
+// ---------------------------------------------------------------- PTX -------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity to complete.
+constexpr long long kWaitLimit = 1ll << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+constexpr int kErrTimeout = 1;
+
+// ------------------------------------------------------- strided pass -------
+// Tile = 2^Q rows (active bits i, stride 2^a) x 2^C contiguous amplitudes j,
+// written dense by the TMA engine at t = j + (i << C).
+// Layout H: register r = i bits QB..QB+4 (QB = Q-5), thread = (j, i bits 0..QB-1):
+//   reading the dense tile gives 32 consecutive amplitudes per warp access.
+// Layout L: register r = i bits 0..4, thread = (j, i bits 5..Q-1).
+// Once the tile is in registers the same buffer serves the transposes in a
+// padded layout (rows of 2^(C+5) amplitudes padded by 2^C), and then receives
+// the next tile while this one is stored: one buffer per CTA, several CTAs
+// per SM, so the warps of other CTAs compute while a CTA waits for its load.
+template <int Q, int C>
+struct TmaGeom {
+  static constexpr int QB = Q - 5;
+  static constexpr int NT = 1 << (Q + C - 5);
+  static constexpr int TILE = 1 << (Q + C);
+  static constexpr int SLOTS = TILE + (TILE >> 5);
+  __host__ __device__ static constexpr int slot(int t) { return t + ((t >> (C + 5)) << C); }
+  static constexpr size_t off_bt = static_cast<size_t>(SLOTS) * 8;
+  static constexpr size_t off_bar = off_bt + 64 * 8;  // room for n + 1 <= 64 entries
+  static constexpr size_t smem = off_bar + 16;
+};
+
+__host__ __device__ constexpr int tma_c(int q) { return (10 - q) > 3 ? (10 - q) : 3; }
+
+// Active bits: i bits 0..4 sit at index bits a1..a1+4 and i bits 5..Q-1 at
+// a2..a2+Q-6 (a2 = a1 + 5 for a contiguous group; a split group, Q = 10 only,
+// takes two 5-bit ranges far apart so that the rows of one tile fall on fewer
+// memory pages).  The tile's fixed bits are [C, a1), [a1+5, a2), [a2+Q-5, n).
+template <int Q, int C, bool WBW>
+__global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ? 1 : (TmaGeom<Q, C>::NT >= 256 ? 3 : 4)))
+    sp_tma_kernel(float2* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, int n, int a1, int a2,
+                  const float2* __restrict__ brow, long long ntiles, int* __restrict__ err) {
+  using G = TmaGeom<Q, C>;
+  constexpr int QB = G::QB;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float2* s_buf = reinterpret_cast<float2*>(smem);
+  float2* s_bt = reinterpret_cast<float2*>(smem + G::off_bt);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + G::off_bar);
+
+  const int tid = threadIdx.x;
+  const int j = tid & ((1 << C) - 1);
+  const int th = tid >> C;
+  // tile index T -> (low, middle, high) fixed-bit fields
+  const int lo_bits = a1 - C, mid_bits = a2 - a1 - 5;
+  const unsigned long long lo_mask = (1ull << lo_bits) - 1ull, mid_mask = (1ull << mid_bits) - 1ull;
+  const long long stride_t = gridDim.x;
+  auto issue = [&](unsigned long long T) {
+    mbar_expect_tx(s_bar, G::TILE * 8u);
+    tma_load_5d(s_buf, &tmap, static_cast<int>((T & lo_mask) << C), 0, static_cast<int>((T >> lo_bits) & mid_mask), 0,
+                static_cast<int>(T >> (lo_bits + mid_bits)), s_bar);
+  };
+
+  if (tid == 0) {
+    mbar_init(s_bar, 1);
+    fence_mbar_init();
+  }
+  if (WBW) {
+    for (int i = tid; i <= n; i += blockDim.x) s_bt[i] = brow[i];
+  }
+  __syncthreads();
+  if (tid == 0 && static_cast<long long>(blockIdx.x) < ntiles) issue(blockIdx.x);
+  const int h_off = j + (th << C);                   // layout H in the dense tile
+  const int sx_h = G::slot(j + (th << C));           // padded slot base, layout H
+  const int sx_l = j + (th << (C + 5)) + (th << C);  // padded slot base, layout L
+  const unsigned long long step_l = 1ull << a1;              // layout L: register r = i bits 0..4
+  const unsigned long long step_h = 1ull << (a2 + QB - 5);    // layout H: register r = i bits QB..QB+4
+
+  int it = 0;
+  for (long long T = blockIdx.x; T < ntiles; T += stride_t, ++it) {
+    const bool ok = mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(err, kErrTimeout);
+      break;
+    }
+    const unsigned long long ut = static_cast<unsigned long long>(T);
+    const unsigned long long xbase = ((ut & lo_mask) << C) | (((ut >> lo_bits) & mid_mask) << (a1 + 5)) |
+                                     ((ut >> (lo_bits + mid_bits)) << (a2 + QB));
+    float2 v[32];
+    {
+      const float2* src = s_buf + h_off;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = src[(r << QB) << C];
+    }
+    reg_wht<0, 5>(v);  // i bits QB..QB+4
+    if (QB > 0) {
+      __syncthreads();  // dense tile fully read
+#pragma unroll
+      for (int r = 0; r < 32; ++r) s_buf[sx_h + G::slot((r << QB) << C)] = v[r];
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = s_buf[sx_l + (r << C)];
+      reg_wht<0, QB>(v);  // i bits 0..QB-1
+    }
+    if (WBW) {
+      // 2^-n exp(-i phi popcount(x)), x the full index
+      const int pc0 = __popcll(xbase) + __popc(j) + __popc(th);
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = cmul(v[r], s_bt[pc0 + __popc(r)]);
+      if (QB > 0) {
+        reg_wht<0, QB>(v);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) s_buf[sx_l + (r << C)] = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = s_buf[sx_h + G::slot((r << QB) << C)];
+      }
+      reg_wht<0, 5>(v);
+    }
+    // the buffer is free: fetch the next tile while this one is stored
+    __syncthreads();
+    if (tid == 0) {
+      const long long Tn = T + stride_t;
+      if (Tn < ntiles) {
+        fence_proxy_async();
+        issue(static_cast<unsigned long long>(Tn));
+      }
+    }
+    if (WBW || QB == 0) {
+      // layout H: i = th + (r << QB); th = i bits 0..QB-1 lie at a1..
+      float2* dst = psi + xbase + j + (static_cast<unsigned long long>(th) << a1);
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        *dst = v[r];
+        dst += step_h;
+      }
+    } else {
+      // layout L: i = r + (th << 5); th = i bits 5..Q-1 lie at a2..
+      float2* dst = psi + xbase + j + (static_cast<unsigned long long>(th) << a2);
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        *dst = v[r];
+        dst += step_l;
+      }
+    }
+  }
+  // leave only when no copy issued by this block is still in flight
+  if (tid == 0) {
+    const long long T = blockIdx.x + static_cast<long long>(it) * stride_t;
+    if (T < ntiles && !mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u)) atomicExch(err, kErrTimeout);
+  }
+}
+
+// ----------------------------------------------------------- low pass -------
+// One 1024-amplitude tile per warp at a time, one buffer per warp: the TMA
+// engine writes the tile dense, the warp reads it into registers (layout X),
+// reuses the buffer for its two padded transposes, then asks for its next tile
+// and folds and counts that tile's clauses while the copy is in flight.
+constexpr int kLpRowT = 33;
+constexpr int kLpSlotsT = 32 * kLpRowT;
+constexpr int kLpTmaWarps = 8;
+
+struct LpTmaLayout {
+  size_t off_pt, off_warp, per_warp, off_bar, total;
+  __host__ __device__ explicit LpTmaLayout(int m) {
+    off_pt = 16u * static_cast<size_t>(m);
+    off_warp = (off_pt + 8u * static_cast<size_t>(m + 1) + 127u) & ~static_cast<size_t>(127);
+    per_warp = (8u * kLpSlotsT + 8u * static_cast<size_t>(m + 16) + 127u) & ~static_cast<size_t>(127);
+    off_bar = off_warp + per_warp * kLpTmaWarps;
+    total = off_bar + 8u * kLpTmaWarps;
+  }
+};
+
+__device__ __forceinline__ void xpose_x2y_t(float2 (&v)[32], float2* __restrict__ s, int lane) {
+  float2* w = s + lane;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) w[kLpRowT * r] = v[r];
+  __syncwarp();
+  const float2* q = s + kLpRowT * lane;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) v[r] = q[r];
+  __syncwarp();
+}
+__device__ __forceinline__ void xpose_y2x_t(float2 (&v)[32], float2* __restrict__ s, int lane) {
+  float2* w = s + kLpRowT * lane;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) w[r] = v[r];
+  __syncwarp();
+  const float2* q = s + lane;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) v[r] = q[kLpRowT * r];
+  __syncwarp();
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
+    lp_tma_kernel(float2* __restrict__ psi, int m, const ClauseLP* __restrict__ cl, const float2* __restrict__ prow,
+                  long long ntiles, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const LpTmaLayout L(m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
+  float2* s_pt = reinterpret_cast<float2*>(smem + L.off_pt);
+  unsigned char* wbase = smem + L.off_warp + L.per_warp * warp;
+  float2* s_buf = reinterpret_cast<float2*>(wbase);  // dense tile, then padded transposes
+  uint2* s_act = reinterpret_cast<uint2*>(wbase + 8u * kLpSlotsT);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp;
+
+  const long long step = static_cast<long long>(gridDim.x) * kLpTmaWarps;
+  const long long first = static_cast<long long>(blockIdx.x) * kLpTmaWarps + warp;
+  if (lane == 0) {
+    mbar_init(s_bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (lane == 0 && first < ntiles) {
+    mbar_expect_tx(s_bar, 8192u);
+    bulk_load(s_buf, psi + (first << kLowBits), 8192u, s_bar);
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) s_pt[i] = prow[i];
+  __syncthreads();
+
+  int nconst = 0, npad = 0;
+  unsigned pl[kPlanes];
+  if (first < ntiles) {
+    fold_tile<KIND != kLpFirst>(s_cl, m, static_cast<unsigned>(first), lane, s_act, nconst, npad);
+    count_active(s_act, npad, 1u << lane, pl);
+  }
+  int it = 0;
+  for (long long tile = first; tile < ntiles; tile += step, ++it) {
+    const bool ok = mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicExch(err, kErrTimeout);
+      break;
+    }
+    float2 v[32];
+    {
+      const float2* src = s_buf + lane;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = src[32 * r];
+    }
+    __syncwarp();
+    if (KIND == kLpFirst) {
+      apply_p_phase(v, pl, nconst, s_pt);
+      reg_wht<0, 5>(v);
+      xpose_x2y_t(v, s_buf, lane);
+      reg_wht<0, 5>(v);
+      xpose_y2x_t(v, s_buf, lane);
+    } else {
+      reg_wht<0, 5>(v);
+      xpose_x2y_t(v, s_buf, lane);
+      reg_wht<0, 5>(v);
+      apply_p_phase(v, pl, nconst, s_pt);
+      if (KIND == kLpMerge) reg_wht<0, 5>(v);
+      xpose_y2x_t(v, s_buf, lane);
+      if (KIND == kLpMerge) reg_wht<0, 5>(v);
+    }
+    const long long tn = tile + step;
+    if (lane == 0 && tn < ntiles) {
+      fence_proxy_async();
+      mbar_expect_tx(s_bar, 8192u);
+      bulk_load(s_buf, psi + (tn << kLowBits), 8192u, s_bar);
+    }
+    float2* g = psi + (tile << kLowBits) + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) g[32 * r] = v[r];
+    if (tn < ntiles) {
+      __syncwarp();
+      fold_tile<KIND != kLpFirst>(s_cl, m, static_cast<unsigned>(tn), lane, s_act, nconst, npad);
+      count_active(s_act, npad, 1u << lane, pl);
+    }
+  }
+  if (lane == 0) {
+    const long long t = first + static_cast<long long>(it) * step;
+    if (t < ntiles && !mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u)) atomicExch(err, kErrTimeout);
+  }
+}
+
+// ------------------------------------------------------------- host ---------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+bool tma_available() { return encode_fn() != nullptr; }
+
+template <int Q, int C>
+static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int a1, int a2, bool wbw,
+                                   const float2* brow, int* err) {
+  using G = TmaGeom<Q, C>;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  constexpr int QB = Q - 5;
+  if (a1 < C || a2 < a1 + 5 || a2 + QB > n || (a2 != a1 + 5 && QB != 5)) return cudaErrorInvalidValue;
+  CUtensorMap map;
+  // dims (innermost first): bits [0,a1), [a1,a1+5), [a1+5,a2), [a2,a2+QB), [a2+QB,n)
+  const cuuint64_t dims[5] = {1ull << a1, 32ull, 1ull << (a2 - a1 - 5), 1ull << QB, 1ull << (n - a2 - QB)};
+  const cuuint64_t strides[4] = {(1ull << a1) * 8ull, (1ull << (a1 + 5)) * 8ull, (1ull << a2) * 8ull,
+                                 (1ull << (a2 + QB)) * 8ull};
+  const cuuint32_t box[5] = {1u << C, 32u, 1u, 1u << QB, 1u};
+  const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+  const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, psi, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const long long ntiles = 1ll << (n - Q - C);
+  auto kern = wbw ? sp_tma_kernel<Q, C, true> : sp_tma_kernel<Q, C, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(G::smem));
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, G::NT, G::smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  long long grid = static_cast<long long>(occ) * lc.num_sms;
+  if (grid > ntiles) grid = ntiles;
+  kern<<<static_cast<unsigned>(grid), G::NT, G::smem, lc.stream>>>(psi, map, n, a1, a2, brow, ntiles, err);
+  return cudaGetLastError();
+}
+
+// Contiguous run per tile row: 2^C amplitudes.  C = 4 (128-byte runs) can be
+// requested for groups whose rows lie far apart in memory (see the pass plan).
+template <int Q>
+static cudaError_t launch_sp_tma(const LaunchCtx& lc, float2* psi, int n, int a1, int a2, bool wbw,
+                                 const float2* brow, int* err, int c_req) {
+  constexpr int C0 = tma_c(Q);
+  if (c_req == 4 && C0 < 4 && a1 >= 4)
+    return launch_sp_tma_c<Q, (C0 < 4 ? 4 : C0)>(lc, psi, n, a1, a2, wbw, brow, err);
+  return launch_sp_tma_c<Q, C0>(lc, psi, n, a1, a2, wbw, brow, err);
+}
+
+template <int KIND>
+static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl,
+                                 const float2* prow, int* err) {
+  const long long ntiles = 1ll << (n - kLowBits);
+  const LpTmaLayout L(m);
+  auto kern = lp_tma_kernel<KIND>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.total));
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLpTmaWarps * 32, L.total);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  long long grid = static_cast<long long>(occ) * lc.num_sms;
+  const long long need = (ntiles + kLpTmaWarps - 1) / kLpTmaWarps;
+  if (grid > need) grid = need;
+  kern<<<static_cast<unsigned>(grid), kLpTmaWarps * 32, L.total, lc.stream>>>(psi, m, cl, prow, ntiles, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
+                            const float2* ptab, const float2* btab, int* err) {
+  const int c_req = p.run_c;
+  switch (p.kind) {
+    case kLpFirst: return launch_lp_tma<kLpFirst>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), err);
+    case kLpMerge: return launch_lp_tma<kLpMerge>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), err);
+    case kLpLast: return launch_lp_tma<kLpLast>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), err);
+    case kSpW:
+    case kSpWBW: {
+      const bool wbw = p.kind == kSpWBW;
+      const float2* brow = btab + static_cast<size_t>(p.brow) * (n + 1);
+      switch (p.q) {
+        case 5: return launch_sp_tma<5>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
+        case 6: return launch_sp_tma<6>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
+        case 7: return launch_sp_tma<7>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
+        case 8: return launch_sp_tma<8>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
+        case 9: return launch_sp_tma<9>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
+        case 10: return launch_sp_tma<10>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace qaa
