@@ -259,6 +259,26 @@ def run_ours(args):
     traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == kernel_src_sha() else None
     gpu_launches = sum(v[0] for v in prof.values())
 
+    # tensor-core split-BF16 Walsh-Hadamard variants on the same workload
+    variants = {}
+    if not args.no_variants:
+        for kind, name in ((1, "bf16x3"), (2, "bf16x2")):
+            vi = q.Instance(n, clauses, stream=stream)
+            vi.set_variant(kind)
+            vi.init_uniform(psi)
+            vk = min(K, 100)
+            vi.evolve(psi, DT * 3, 3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            vi.evolve(psi, DT * vk, vk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            vms = e0.elapsed_time(e1)
+            variants[name] = {"steps_per_s": vk / (vms / 1e3), "ms_per_step": vms / vk, "steps": vk,
+                              "hbm_gbs": passes_per_step * 2 * state_bytes * vk / (vms / 1e3) / 1e9}
+            vi.close()
+
     # e2e: a full solve through the public API with the instance in host memory
     e2e = None
     if not args.no_e2e:
@@ -304,6 +324,7 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "clocks": clk.summary(),
             "e2e": e2e,
+            "precision_variants": variants,
             "cpu_baseline": cpu,
             "final": {"norm": obs["norm"], "ground_prob": obs["ground_prob"]},
         }
@@ -322,6 +343,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the tensor-core WHT variants")
     ap.add_argument("--instance", default=INSTANCE,
                     help="committed instance to evolve (default: the n=30 benchmark instance); smaller ones are "
                          "for profiling captures")

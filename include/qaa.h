@@ -88,10 +88,15 @@ int qaa_destroy(qaa_handle h);
 int qaa_set_stream(qaa_handle h, void* cuda_stream);
 
 /*
- * qaa_set_variant -- choose the Walsh-Hadamard implementation.
+ * qaa_set_variant -- choose the Walsh-Hadamard implementation of the
+ * streaming passes (n >= 15; the on-chip path for n <= 14 is always FP32).
  *   wht_kind 0: FP32 CUDA-core butterflies (default).
- *   q        reserved for the qubits-per-pass choice; 0 = automatic.
- * Returns QAA_E_ARG for an unknown kind.
+ *            1: tensor cores, 16 x 16 Hadamard blocks on BF16 operands with the
+ *               amplitude split into three BF16 parts (hi + mid + lo), FP32
+ *               accumulation: about FP32 accuracy.
+ *            2: as 1 with two parts (hi + lo): about 16 mantissa bits.
+ *   q        reserved for the qubits-per-pass choice; only 0 (automatic).
+ * Returns QAA_E_ARG for an unknown kind or q != 0.
  */
 int qaa_set_variant(qaa_handle h, int wht_kind, int q);
 

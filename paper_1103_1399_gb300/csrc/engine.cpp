@@ -333,8 +333,10 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
     } else {
       build_passes(h, k0, k1, c0, c1, passes);
       const bool tma = h->use_tma;
+      const int tc_parts = h->wht_kind == 1 ? 3 : (h->wht_kind == 2 ? 2 : 0);
       for (const qaa::Pass& ps : passes)
         QAA_CK(timed(h, ps.kind, [&] {
+          if (tc_parts) return qaa::launch_pass_tc(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab, tc_parts);
           return tma ? qaa::launch_pass_tma(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab, h->d_err)
                      : qaa::launch_pass(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab);
         }));
@@ -464,7 +466,7 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream) {
 
 int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (!h) return fail(QAA_E_ARG, "null handle");
-  if (wht_kind != 0) return fail(QAA_E_ARG, "unknown wht_kind");
+  if (wht_kind < 0 || wht_kind > 2) return fail(QAA_E_ARG, "unknown wht_kind (0 = FP32, 1 = BF16x3, 2 = BF16x2)");
   if (q != 0) return fail(QAA_E_ARG, "only automatic qubits-per-pass (q = 0) is available");
   h->wht_kind = wht_kind;
   return QAA_OK;
@@ -556,7 +558,9 @@ int qaa_describe_plan(qaa_handle h, char* buf, size_t len) {
   } else {
     const int ng = static_cast<int>(h->strided.size());
     const int pg = h->phase_group < ng ? h->phase_group : ng - 1;
-    d = "streaming, " + std::string(h->use_tma ? "TMA" : "classic") + " loads; low pass bits [0,10) W.P.W";
+    const char* wk = h->wht_kind == 1 ? "tensor-core BF16x3" : (h->wht_kind == 2 ? "tensor-core BF16x2" : "FP32");
+    d = "streaming, " + std::string(h->wht_kind ? "plain" : (h->use_tma ? "TMA" : "classic")) + " loads, " + wk +
+        " WHT; low pass bits [0,10) W.P.W";
     for (int i = 0; i < ng; ++i) {
       const Group& g = h->strided[i];
       int c = i == pg ? 0 : 4;
@@ -564,7 +568,7 @@ int qaa_describe_plan(qaa_handle h, char* buf, size_t len) {
       d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";
       if (g.q > 5) d += "+[" + std::to_string(g.a2) + "," + std::to_string(g.a2 + g.q - 5) + ")";
       d += i == pg ? " W.B.W" : " W";
-      if (h->use_tma) d += c == 4 ? " 128B runs" : " 64B runs";
+      if (h->use_tma && !h->wht_kind) d += c == 4 ? " 128B runs" : " 64B runs";
     }
     d += "; " + std::to_string(2 * (ng + 1) - 2) + " HBM round trips per step";
   }

@@ -94,6 +94,12 @@ bool tma_available();
 cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
                             const float2* ptab, const float2* btab, int* err);
 
+// Tensor-core variant (tc_kernels.cu): the Walsh-Hadamard transforms of every
+// streaming pass as 16 x 16 Hadamard blocks on BF16-split operands (parts = 3:
+// hi + mid + lo, parts = 2: hi + lo) with FP32 accumulation.
+cudaError_t launch_pass_tc(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
+                           const float2* ptab, const float2* btab, int parts);
+
 // Store a message for qaa_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

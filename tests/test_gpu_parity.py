@@ -257,3 +257,35 @@ def test_observables_match_oracle(q, torch, n):
     assert inst.norm(psi) == o["norm"]
     # fixed reduction order: bit-identical on repeat
     assert inst.observables(psi) == o
+
+
+# ------------------------------------------------ tensor-core WHT variant ---
+# BF16x3 (hi + mid + lo, FP32 accumulation; hi and the small parts in separate
+# accumulators) is held to the FP32 bar; BF16x2 to the BF16-split bar of 1e-3.
+# Measured at n = 20, T = 10, 200 steps: 6.1e-7 (x3) and 2.4e-5 (x2).
+TC_CASES = [(15, 3.0, 20), (17, 3.0, 12), (20, 10.0, 200), (21, 1.0, 4)]
+
+
+@pytest.mark.parametrize("kind,amp_tol,prob_tol", [(1, AMP_TOL, PROB_TOL), (2, 1e-3, 1e-4)], ids=["bf16x3", "bf16x2"])
+@pytest.mark.parametrize("n,T,K", TC_CASES, ids=[f"n{c[0]}-K{c[2]}" for c in TC_CASES])
+def test_tensor_core_variant_matches_oracle(q, torch, kind, amp_tol, prob_tol, n, T, K):
+    cl = satgen.load_instance("planted_n20_s0")["clauses"] if n == 20 else satgen.planted_instance(n, 11)["clauses"]
+    e = oracle.violated_counts(n, cl)
+    ref = oracle.evolve_strang(n, cl, T, K, energies=e)
+    inst = q.Instance(n, cl)
+    inst.set_variant(kind)
+    assert "tensor-core" in inst.describe_plan()
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    inst.init_uniform(psi)
+    inst.evolve(psi, T, K)
+    o = inst.observables(psi)
+    assert np.max(np.abs(to_np(psi) - ref)) <= amp_tol
+    assert abs(o["ground_prob"] / o["norm"] - oracle.success_prob(ref, e)) <= prob_tol
+
+
+def test_variant_argument_checks(q, torch):
+    inst = q.Instance(16, [[1, 2, 3]])
+    with pytest.raises(q.QaaError):
+        inst.set_variant(3)
+    with pytest.raises(q.QaaError):
+        inst.set_variant(0, 7)
