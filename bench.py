@@ -194,6 +194,101 @@ def run_reference(args):
     }))
 
 
+# ------------------------------------------------------------- serving --------
+SERVE_DT = 0.05
+
+
+def _gen_instance(args):
+    n, seed = args
+    import satgen
+    return satgen.planted_instance(n, seed)["clauses"]
+
+
+def serving_workload(count, seed=0):
+    """The batched-serving mix: n ~ U{10..22}, T ~ U[5, 80], dt = 0.05, one
+    independent planted unique-solution instance per request (generated in a
+    spawn process pool)."""
+    import multiprocessing as mp
+    import satgen
+    reqs = satgen.serving_requests(count, seed=seed)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        clauses = pool.map(_gen_instance, [(n, s) for _, n, _, s in reqs], chunksize=8)
+    return [(n, cl, T, max(1, int(round(T / SERVE_DT)))) for (_, n, T, _), cl in zip(reqs, clauses)]
+
+
+def _pct(v, p):
+    import numpy as np
+    return float(np.percentile(np.asarray(v), p)) if v else None
+
+
+def run_serving(q, torch, work, rate_factor=0.7):
+    out = {"requests": len(work), "dt": SERVE_DT, "mix": "n ~ U{10..22}, T ~ U[5,80], planted unique-solution"}
+    # baseline: one launch sequence per instance, one after another (handle API)
+    t0 = time.perf_counter()
+    lat = []
+    for n, cl, T, K in work:
+        with q.Instance(n, cl) as inst:
+            psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+            inst.init_uniform(psi)
+            inst.evolve(psi, T, K)
+            inst.observables(psi)
+        lat.append(time.perf_counter() - t0)
+    base_s = time.perf_counter() - t0
+    out["one_launch_per_instance"] = {"solves_per_s": len(work) / base_s, "p50_ms": 1e3 * _pct(lat, 50),
+                                      "p99_ms": 1e3 * _pct(lat, 99), "makespan_s": base_s,
+                                      "what": "all requests at t=0, solved one at a time: qaa_create, init, "
+                                              "evolve, observables, destroy"}
+    # continuous batching, all requests at t=0 (capacity)
+    with q.Server(max_slots=1024) as srv:
+        t0 = time.perf_counter()
+        tickets = [srv.submit(n, cl, T, K) for n, cl, T, K in work]
+        res = _wait_all(srv, tickets)
+        cap_s = time.perf_counter() - t0
+        st = srv.stats()
+    lat = [r["t_done"] - r["t_submit"] for r in res]
+    out["continuous_batching"] = {"solves_per_s": len(work) / cap_s, "p50_ms": 1e3 * _pct(lat, 50),
+                                  "p99_ms": 1e3 * _pct(lat, 99), "makespan_s": cap_s,
+                                  "ok": sum(1 for r in res if r["status"] == 0), "server": st,
+                                  "arrivals": "all at t=0"}
+    # Poisson arrivals at rate_factor x the one-launch-per-instance throughput
+    rate = rate_factor * len(work) / base_s
+    rng = __import__("numpy").random.default_rng(1)
+    arrivals = __import__("numpy").cumsum(rng.exponential(1.0 / rate, size=len(work)))
+    with q.Server(max_slots=1024) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for (n, cl, T, K), ta in zip(work, arrivals):
+            dt_wait = ta - (time.perf_counter() - t0)
+            if dt_wait > 0:
+                time.sleep(dt_wait)
+            tickets.append(srv.submit(n, cl, T, K))
+        res = _wait_all(srv, tickets)
+        poi_s = time.perf_counter() - t0
+    lat = [r["t_done"] - r["t_submit"] for r in res]
+    out["poisson"] = {"rate_per_s": rate, "solves_per_s": len(work) / poi_s, "p50_ms": 1e3 * _pct(lat, 50),
+                      "p99_ms": 1e3 * _pct(lat, 99), "makespan_s": poi_s,
+                      "ok": sum(1 for r in res if r["status"] == 0)}
+    out["solves_per_s"] = out["continuous_batching"]["solves_per_s"]
+    out["p50_ms"] = out["poisson"]["p50_ms"]
+    out["p99_ms"] = out["poisson"]["p99_ms"]
+    return out
+
+
+def _wait_all(srv, tickets, timeout=600.0):
+    pending, res, t0 = set(tickets), {}, time.perf_counter()
+    while pending:
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                res[t] = r
+                pending.discard(t)
+        if time.perf_counter() - t0 > timeout:
+            raise RuntimeError("serving requests did not finish")
+        time.sleep(0.0005)
+    return [res[t] for t in tickets]
+
+
 # ------------------------------------------------------------- GPU arm --------
 def run_ours(args):
     import torch
@@ -295,6 +390,10 @@ def run_ours(args):
                "what": "qaa_create (clause tables host->device) + init + evolve K steps + observables "
                        "(device->host), timed on the host"}
 
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        serving = run_serving(q, torch, serving_workload(args.serving_requests))
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         t_e, t_step = oracle_step_sample(20, 24)
@@ -325,6 +424,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
             "precision_variants": variants,
+            "serving": serving,
             "cpu_baseline": cpu,
             "final": {"norm": obs["norm"], "ground_prob": obs["ground_prob"]},
         }
@@ -344,6 +444,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the tensor-core WHT variants")
+    ap.add_argument("--serving-requests", type=int, default=1024,
+                    help="requests in the batched-serving measurement (0 skips it)")
     ap.add_argument("--instance", default=INSTANCE,
                     help="committed instance to evolve (default: the n=30 benchmark instance); smaller ones are "
                          "for profiling captures")

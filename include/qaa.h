@@ -204,6 +204,61 @@ int qaa_observables_noalloc(int n, const int32_t* clauses, int m, const void* ps
                             qaa_obs* out);
 
 /*
+ * Serving: a loop that evolves requests of different n and T as they arrive.
+ * A library addition built on the same kernels (the paper evolves one instance
+ * at a time).  Requests keep their states resident in a device arena that the
+ * server reserves once, are admitted when their memory block and a result slot
+ * are free, run in continuous batches (every admitted request with n <= 14 in
+ * one launch of the batched on-chip evolver; larger ones as streaming passes on
+ * a pool of streams, overlapped), and report host-clock timestamps for latency.
+ * Each request evolves from the uniform superposition over T with `steps`
+ * Strang steps (as qaa_evolve) and returns the observables of the final state.
+ * All functions are thread safe.
+ */
+typedef struct qaa_server qaa_server;
+
+typedef struct {
+  double success_prob;   /* sum over E(x) = 0 of |psi_x|^2                        */
+  double energy;         /* <H_P> = <H(1)>                                         */
+  double norm;           /* sum |psi_x|^2                                          */
+  double expect_hb;      /* <H_B>                                                  */
+  int64_t ground_count;  /* number of assignments with E(x) = 0                    */
+  double t_submit;       /* seconds on the server's steady clock                   */
+  double t_admit;        /* memory granted (-1 if never admitted)                  */
+  double t_done;         /* results available                                      */
+  int n;
+  int64_t steps;
+  int status;            /* QAA_OK, QAA_E_STATE (cancelled), QAA_E_CUDA, QAA_E_TIMEOUT */
+} qaa_result;
+
+typedef struct {
+  size_t arena_bytes;        /* device memory reserved for request states         */
+  size_t peak_used_bytes;    /* largest amount of it in use at once               */
+  int64_t batches;           /* on-chip batch launches                            */
+  int64_t batched_requests;  /* requests run in those batches                     */
+  int64_t streamed_requests; /* requests run as streaming passes                  */
+} qaa_server_info;
+
+/* hbm_budget_bytes: arena size (0 = free memory minus 4 GiB, at most 64 GiB);
+ * max_slots: requests admitted at once (1..65536).  Starts the worker threads. */
+int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out);
+/* Copies the instance (as qaa_create) and returns a ticket at once.  QAA_E_NOMEM
+ * if the request can never fit in the arena; QAA_E_ARG for invalid input. */
+int qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, int64_t steps, uint64_t* ticket);
+/* QAA_PENDING until done, then QAA_OK with *out filled (its status field tells
+ * how the request ended).  Results stay available until the server is destroyed. */
+int qaa_poll(qaa_server* s, uint64_t ticket, qaa_result* out);
+/* Cancel a request not yet admitted (QAA_E_STATE once admitted). */
+int qaa_cancel(qaa_server* s, uint64_t ticket);
+int qaa_server_stats(qaa_server* s, qaa_server_info* out);
+/* Host-side fault injection for tests: fault 1 delays the worker thread by
+ * param milliseconds once; fault 2 fails the next admitted request (status
+ * QAA_E_CUDA) without touching the device. */
+int qaa_server_inject(qaa_server* s, int fault, int param);
+/* Finishes running requests, cancels queued ones, releases everything. */
+int qaa_server_destroy(qaa_server* s);
+
+/*
  * Launch profiling (tracing).  When enabled, the handle records a pair of CUDA
  * events on its stream around every kernel it launches and accumulates, per
  * kernel kind, the number of launches and their summed device time.

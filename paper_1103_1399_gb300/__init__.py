@@ -7,7 +7,7 @@ imports without the library.
 """
 
 _EXPORTS = ("Instance", "QaaError", "lib", "flatten_clauses", "SIGNATURES", "MAX_QUBITS", "MAX_CLAUSES",
-            "LIB_PATH", "Obs", "KERNEL_KINDS")
+            "LIB_PATH", "Obs", "KERNEL_KINDS", "Server")
 
 __all__ = list(_EXPORTS)
 

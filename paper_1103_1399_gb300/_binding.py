@@ -32,6 +32,18 @@ class Obs(ctypes.Structure):
                 ("ground_prob", ctypes.c_double), ("ground_count", ctypes.c_int64)]
 
 
+class Result(ctypes.Structure):
+    _fields_ = [("success_prob", ctypes.c_double), ("energy", ctypes.c_double), ("norm", ctypes.c_double),
+                ("expect_hb", ctypes.c_double), ("ground_count", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("n", ctypes.c_int),
+                ("steps", ctypes.c_int64), ("status", ctypes.c_int)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("peak_used_bytes", ctypes.c_size_t), ("batches", ctypes.c_int64),
+                ("batched_requests", ctypes.c_int64), ("streamed_requests", ctypes.c_int64)]
+
+
 _c_int, _vp, _dbl, _i64 = ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_int64
 
 # name -> (restype, argtypes); the exported surface of include/qaa.h
@@ -53,6 +65,13 @@ SIGNATURES = {
     "qaa_hp_diagonal": (_c_int, [_vp, _vp]),
     "qaa_observables_noalloc": (_c_int, [_c_int, _vp, _c_int, _vp, _vp, ctypes.POINTER(Obs)]),
     "qaa_describe_plan": (_c_int, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
+    "qaa_server_create": (_c_int, [ctypes.c_size_t, _c_int, ctypes.POINTER(_vp)]),
+    "qaa_submit": (_c_int, [_vp, _c_int, _vp, _c_int, _dbl, _i64, ctypes.POINTER(ctypes.c_uint64)]),
+    "qaa_poll": (_c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "qaa_cancel": (_c_int, [_vp, ctypes.c_uint64]),
+    "qaa_server_stats": (_c_int, [_vp, ctypes.POINTER(ServerInfo)]),
+    "qaa_server_inject": (_c_int, [_vp, _c_int, _c_int]),
+    "qaa_server_destroy": (_c_int, [_vp]),
     "qaa_profile_enable": (_c_int, [_vp, _c_int]),
     "qaa_profile_reset": (_c_int, [_vp]),
     "qaa_profile_read": (_c_int, [_vp, _c_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
@@ -225,3 +244,56 @@ class Instance:
         if hasattr(out, "numel") and out.numel() != (1 << self.n):
             raise ValueError("out must have 2^n elements")
         _check(lib.qaa_hp_diagonal(self._h, _ptr(out)))
+
+
+class Server:
+    """Continuous-batching evolve server on the current device (qaa_server_*)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_slots=256):
+        h = ctypes.c_void_p()
+        _check(lib.qaa_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+        self._s = h
+
+    def submit(self, n, clauses, T, steps):
+        buf, m = flatten_clauses(clauses)
+        t = ctypes.c_uint64()
+        _check(lib.qaa_submit(self._s, int(n), ctypes.cast(buf, ctypes.c_void_p), m, float(T), int(steps),
+                              ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else a dict of the result (status 0 = QAA_OK)."""
+        r = Result()
+        st = lib.qaa_poll(self._s, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if st == QAA_PENDING:
+            return None
+        _check(st)
+        return {f: getattr(r, f) for f, _ in Result._fields_}
+
+    def cancel(self, ticket):
+        _check(lib.qaa_cancel(self._s, ctypes.c_uint64(ticket)))
+
+    def stats(self):
+        i = ServerInfo()
+        _check(lib.qaa_server_stats(self._s, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in ServerInfo._fields_}
+
+    def inject(self, fault, param=0):
+        _check(lib.qaa_server_inject(self._s, int(fault), int(param)))
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib.qaa_server_destroy(self._s)
+            self._s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,16 +1,6 @@
-// Host engine behind the C ABI of include/qaa.h: clause encoding, pass
-// planning, phase-table scheduling and kernel launch order.
-//
-// Clause encoding (Sec. 2.2 clauses, Sec. 4.3 energy): a clause over literals
-// l_1..l_k is violated exactly when every literal is false, i.e. when
-// (x & mask) == viol with mask the bits of its variables and viol the value of
-// each variable that falsifies its literal (0 for x_i, 1 for NOT x_i).
-//
-// Pass plan for n >= 15 (state streamed from HBM): G1 = bits 0..9 (low pass),
-// the remaining n-10 bits split into 1..3 strided groups of 5..10 bits.  Per
-// Strang step: top group W B W, the middle groups downwards, the low pass
-// W P W (merging the half phases of two steps), the middle groups upwards:
-// 2g-2 HBM round trips for g groups.  n <= 14 runs entirely on chip.
+// Handle API of include/qaa.h: device buffers of one instance, phase-table
+// scheduling in chunks of steps, kernel launch order (the pass plan comes from
+// plan.cpp), observables and launch profiling.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -20,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "engine_internal.h"
 #include "qaa.h"
 #include "qaa_internal.cuh"
 
@@ -39,18 +30,13 @@ int fail(int code, const std::string& msg) {
       return fail(QAA_E_CUDA, std::string(#expr) + " failed: " + cudaGetErrorString(e_)); \
   } while (0)
 
-constexpr long long kChunkSteps = 1024;
-
-struct Group {
-  int a, q, a2;  // active bits [a, a+5) and [a2, a2+q-5); a2 == a + 5 for a contiguous group
-};
+using qaa::kChunkSteps;
 
 }  // namespace
 
 struct qaa_ctx {
   int n = 0, m = 0, device = 0, num_sms = 0;
   cudaStream_t stream = nullptr;
-  int wht_kind = 0;
   std::vector<qaa::ClauseMV> mv;
   std::vector<qaa::ClauseLP> lp;
   qaa::ClauseMV* d_mv = nullptr;
@@ -64,11 +50,7 @@ struct qaa_ctx {
   double* d_res = nullptr;
   double* h_res = nullptr;  // pinned
   int* d_err = nullptr;     // set by kernels whose bounded waits expired
-  bool use_tma = true;      // TMA-pipelined streaming passes (QAA_PASSES=classic selects the others)
-  int phase_group = 1 << 20;  // strided group hosting the popcount phase (default: the top one)
-  bool split_groups = true;   // recombine two 10-bit strided groups (see plan_groups)
-  int run128_groups = -1;     // bit i set: strided group i uses 128-byte runs (-1: default policy)
-  std::vector<Group> strided;  // ascending bit order; back() is the top group
+  qaa::PassPlan plan;
   // launch profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
@@ -82,84 +64,6 @@ struct qaa_ctx {
 };
 
 namespace {
-
-int encode(qaa_ctx* h, const int32_t* clauses) {
-  h->mv.resize(static_cast<size_t>(h->m));
-  h->lp.resize(static_cast<size_t>(h->m));
-  for (int c = 0; c < h->m; ++c) {
-    unsigned long long mask = 0, viol = 0;
-    int width = 0;
-    for (int k = 0; k < 3; ++k) {
-      const int32_t lit = clauses[3 * c + k];
-      if (lit == 0) continue;
-      const long long a = lit < 0 ? -static_cast<long long>(lit) : lit;
-      if (a > h->n) return fail(QAA_E_ARG, "clause " + std::to_string(c) + ": literal beyond n");
-      const unsigned long long bit = 1ull << (a - 1);
-      if (mask & bit) return fail(QAA_E_ARG, "clause " + std::to_string(c) + ": variable repeated in a clause");
-      mask |= bit;
-      if (lit < 0) viol |= bit;
-      ++width;
-    }
-    if (width == 0) return fail(QAA_E_ARG, "clause " + std::to_string(c) + ": no literals");
-    h->mv[c] = {mask, viol};
-    qaa::ClauseLP e;
-    e.hi_mask = static_cast<unsigned>(mask >> qaa::kLowBits);
-    e.hi_viol = static_cast<unsigned>(viol >> qaa::kLowBits);
-    unsigned p0 = 0, p5 = 0;
-    const unsigned m0 = static_cast<unsigned>(mask & 31u), v0 = static_cast<unsigned>(viol & 31u);
-    const unsigned m5 = static_cast<unsigned>((mask >> 5) & 31u), v5 = static_cast<unsigned>((viol >> 5) & 31u);
-    for (unsigned j = 0; j < 32; ++j) {
-      if ((j & m0) == v0) p0 |= 1u << j;
-      if ((j & m5) == v5) p5 |= 1u << j;
-    }
-    e.pat0 = p0;
-    e.pat5 = p5;
-    h->lp[c] = e;
-  }
-  return QAA_OK;
-}
-
-// Strided groups above the low pass: the n-10 remaining bits in groups of 5..10
-// (as equal as possible), or the sizes given in QAA_GROUP_BITS ("10,8"), a
-// tuning override.
-void plan_groups(qaa_ctx* h) {
-  h->strided.clear();
-  if (h->n <= qaa::kOnchipMaxBits) return;
-  const int rest = h->n - qaa::kLowBits;
-  std::vector<int> sizes;
-  if (const char* gb = std::getenv("QAA_GROUP_BITS")) {
-    int sum = 0;
-    bool ok = true;
-    for (const char* p = gb; *p;) {
-      const int q = std::atoi(p);
-      if (q < 5 || q > 10) ok = false;
-      sizes.push_back(q);
-      sum += q;
-      while (*p && *p != ',') ++p;
-      if (*p == ',') ++p;
-    }
-    if (!ok || sum != rest) sizes.clear();
-  }
-  if (sizes.empty()) {
-    const int ng = (rest + 9) / 10;
-    const int base = rest / ng, extra = rest % ng;
-    for (int g = 0; g < ng; ++g) sizes.push_back(base + (g < extra ? 1 : 0));
-  }
-  int a = qaa::kLowBits;
-  for (int q : sizes) {
-    h->strided.push_back({a, q, a + 5});
-    a += q;
-  }
-  // Two 10-bit strided groups [10,20) and [20,30): recombine them as
-  // {10..14, 25..29} and {15..24}.  With [20,30) as one group every tile has
-  // 1024 rows 8 MiB apart, each on its own memory page; recombined, a tile
-  // spans at most 128 pages.
-  if (h->split_groups && h->strided.size() == 2 && h->strided[0].q == 10 && h->strided[1].q == 10) {
-    const int b = qaa::kLowBits;
-    h->strided[0] = {b, 10, b + 15};
-    h->strided[1] = {b + 5, 10, b + 10};
-  }
-}
 
 qaa::LaunchCtx lctx(const qaa_ctx* h) { return {h->stream, h->num_sms}; }
 
@@ -228,46 +132,6 @@ int ensure_tab(qaa_ctx* h, size_t entries) {
   return QAA_OK;
 }
 
-// The popcount phase B needs every qubit in the Hadamard basis, so it is applied
-// inside the pass of whichever strided group is transformed last (the "phase
-// group"); the others are transformed before it (in ascending order) and after
-// it (descending).
-void build_passes(const qaa_ctx* h, long long k0, long long k1, long long c0, long long c1,
-                  std::vector<qaa::Pass>& out) {
-  out.clear();
-  const int ng = static_cast<int>(h->strided.size());
-  const int pg = h->phase_group < ng ? h->phase_group : ng - 1;
-  const Group top = h->strided[pg];
-  // Contiguous run per tile row: 128 bytes for the plain strided passes, 64
-  // bytes (more CTAs per SM) for the heavier pass that hosts the phase.
-  auto runc = [&](int i) {
-    if (h->run128_groups >= 0) return ((h->run128_groups >> i) & 1) ? 4 : 0;
-    return i == pg ? 0 : 4;
-  };
-  auto mid_up = [&]() {
-    for (int i = 0; i < ng; ++i)
-      if (i != pg) out.push_back({qaa::kSpW, h->strided[i].a, h->strided[i].q, 0, runc(i), 0, h->strided[i].a2});
-  };
-  auto mid_down = [&]() {
-    for (int i = ng - 1; i >= 0; --i)
-      if (i != pg) out.push_back({qaa::kSpW, h->strided[i].a, h->strided[i].q, 0, runc(i), 0, h->strided[i].a2});
-  };
-  if (c0 == k0) {
-    out.push_back({qaa::kLpFirst, 0, 0, 0, 0, 0, 0});
-    mid_up();
-  }
-  for (long long k = c0; k < c1; ++k) {
-    out.push_back({qaa::kSpWBW, top.a, top.q, 0, runc(pg), static_cast<int>(k - c0), top.a2});
-    mid_down();
-    if (k == k1 - 1) {
-      out.push_back({qaa::kLpLast, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0});
-    } else {
-      out.push_back({qaa::kLpMerge, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0});
-      mid_up();
-    }
-  }
-}
-
 int check_handle(qaa_ctx* h) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   QAA_CK(cudaSetDevice(h->device));
@@ -331,14 +195,10 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
         return qaa::launch_onchip(lc, p, h->n, h->m, h->d_mv, ptab, btab, static_cast<int>(c1 - c0), c0 == k0);
       }));
     } else {
-      build_passes(h, k0, k1, c0, c1, passes);
-      const bool tma = h->use_tma;
-      const int tc_parts = h->wht_kind == 1 ? 3 : (h->wht_kind == 2 ? 2 : 0);
+      qaa::build_passes(h->plan, k0, k1, c0, c1, passes);
       for (const qaa::Pass& ps : passes)
         QAA_CK(timed(h, ps.kind, [&] {
-          if (tc_parts) return qaa::launch_pass_tc(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab, tc_parts);
-          return tma ? qaa::launch_pass_tma(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab, h->d_err)
-                     : qaa::launch_pass(lc, ps, p, h->n, h->m, h->d_lp, ptab, btab);
+          return qaa::launch_planned_pass(lc, h->plan, ps, p, h->m, h->d_lp, ptab, btab, h->d_err);
         }));
     }
   }
@@ -395,10 +255,13 @@ int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out) {
   if (!h) return fail(QAA_E_NOMEM, "host allocation failed");
   h->n = n;
   h->m = m;
-  int st = encode(h, clauses);
-  if (st) {
-    delete h;
-    return st;
+  {
+    std::string err;
+    const int st = qaa::encode_clauses(n, clauses, m, h->mv, h->lp, err);
+    if (st) {
+      delete h;
+      return fail(st, err);
+    }
   }
   auto cleanup = [&](int code, const std::string& msg) {
     qaa_destroy(h);
@@ -417,17 +280,7 @@ int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out) {
     return cleanup(QAA_E_NOMEM, "cannot allocate clause tables");
   }
   if (cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess) return cleanup(QAA_E_CUDA, "cannot clear error word");
-  {
-    const char* env = std::getenv("QAA_PASSES");
-    h->use_tma = qaa::tma_available() && !(env && std::strcmp(env, "classic") == 0);
-    const char* pg = std::getenv("QAA_PHASE_GROUP");
-    if (pg) h->phase_group = std::atoi(pg);
-    const char* rg = std::getenv("QAA_RUN128_GROUPS");
-    if (rg) h->run128_groups = std::atoi(rg);
-    const char* sg = std::getenv("QAA_SPLIT_GROUPS");
-    h->split_groups = h->use_tma && !(sg && std::atoi(sg) == 0);
-    plan_groups(h);
-  }
+  qaa::make_plan(n, h->plan);
   if (m > 0) {
     if (cudaMemcpy(h->d_mv, h->mv.data(), m * sizeof(qaa::ClauseMV), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_lp, h->lp.data(), m * sizeof(qaa::ClauseLP), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -468,7 +321,7 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   if (wht_kind < 0 || wht_kind > 2) return fail(QAA_E_ARG, "unknown wht_kind (0 = FP32, 1 = BF16x3, 2 = BF16x2)");
   if (q != 0) return fail(QAA_E_ARG, "only automatic qubits-per-pass (q = 0) is available");
-  h->wht_kind = wht_kind;
+  h->plan.wht_kind = wht_kind;
   return QAA_OK;
 }
 
@@ -552,26 +405,7 @@ int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev) {
 int qaa_describe_plan(qaa_handle h, char* buf, size_t len) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   if (!buf || len == 0) return fail(QAA_E_ARG, "buf is null or empty");
-  std::string d;
-  if (h->n <= qaa::kOnchipMaxBits) {
-    d = "on-chip: whole run in one CTA's shared memory (n=" + std::to_string(h->n) + ")";
-  } else {
-    const int ng = static_cast<int>(h->strided.size());
-    const int pg = h->phase_group < ng ? h->phase_group : ng - 1;
-    const char* wk = h->wht_kind == 1 ? "tensor-core BF16x3" : (h->wht_kind == 2 ? "tensor-core BF16x2" : "FP32");
-    d = "streaming, " + std::string(h->wht_kind ? "plain" : (h->use_tma ? "TMA" : "classic")) + " loads, " + wk +
-        " WHT; low pass bits [0,10) W.P.W";
-    for (int i = 0; i < ng; ++i) {
-      const Group& g = h->strided[i];
-      int c = i == pg ? 0 : 4;
-      if (h->run128_groups >= 0) c = ((h->run128_groups >> i) & 1) ? 4 : 0;
-      d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";
-      if (g.q > 5) d += "+[" + std::to_string(g.a2) + "," + std::to_string(g.a2 + g.q - 5) + ")";
-      d += i == pg ? " W.B.W" : " W";
-      if (h->use_tma && !h->wht_kind) d += c == 4 ? " 128B runs" : " 64B runs";
-    }
-    d += "; " + std::to_string(2 * (ng + 1) - 2) + " HBM round trips per step";
-  }
+  const std::string d = qaa::describe_plan(h->plan);
   std::strncpy(buf, d.c_str(), len - 1);
   buf[len - 1] = '\0';
   return QAA_OK;

@@ -1,0 +1,57 @@
+// Host-side pieces shared by the handle API (engine.cpp) and the serving loop
+// (serve.cpp): clause encoding, pass planning and launch of a planned pass.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "qaa_internal.cuh"
+
+namespace qaa {
+
+// Clause c over literals l_1..l_k (Sec. 2.2) is violated exactly when every
+// literal is false (Sec. 4.3 counts such clauses): (x & mask) == viol, with
+// mask the bits of its variables and viol, per variable, the value that makes
+// its literal false.  Returns 0, or a nonzero code with a message.
+int encode_clauses(int n, const int32_t* lits, int m, std::vector<ClauseMV>& mv, std::vector<ClauseLP>& lp,
+                   std::string& err);
+
+struct Group {
+  int a, q, a2;  // active bits [a, a+5) and [a2, a2+q-5); a2 == a + 5 for a contiguous group
+};
+
+// How an n-qubit state is evolved: on chip (n <= 14) or by streaming passes.
+struct PassPlan {
+  int n = 0;
+  bool onchip = false;
+  bool use_tma = true;       // TMA-pipelined passes (QAA_PASSES=classic: plain loads)
+  int wht_kind = 0;          // 0 FP32 butterflies, 1/2 tensor-core BF16x3/x2
+  std::vector<Group> strided;  // ascending bit order
+  int phase_group = 0;         // strided group whose pass fuses W B W
+  std::vector<int> run_c;      // per strided group: 4 = 128-byte runs, 0 = default
+};
+
+// Default plan for n, with the tuning overrides QAA_PASSES, QAA_SPLIT_GROUPS,
+// QAA_PHASE_GROUP, QAA_RUN128_GROUPS and QAA_GROUP_BITS read from the
+// environment.
+void make_plan(int n, PassPlan& plan);
+
+// Passes for steps c0 <= k < c1 of the range [k0, k1): P rows are relative to
+// the chunk (row k + 1 - c0 ends step k), B rows likewise (row k - c0).
+void build_passes(const PassPlan& plan, long long k0, long long k1, long long c0, long long c1,
+                  std::vector<Pass>& out);
+
+std::string describe_plan(const PassPlan& plan);
+
+// Launch one pass with the kernel family the plan selects.
+cudaError_t launch_planned_pass(const LaunchCtx& lc, const PassPlan& plan, const Pass& p, float2* psi, int m,
+                                const ClauseLP* cl, const float2* ptab, const float2* btab, int* err);
+
+constexpr long long kChunkSteps = 1024;
+
+// Bytes of phase tables for a chunk of `chunk` steps.
+inline size_t table_entries(int n, int m, long long chunk) {
+  return static_cast<size_t>(chunk + 1) * static_cast<size_t>(m + 1) + static_cast<size_t>(chunk) * (n + 1);
+}
+
+}  // namespace qaa

@@ -207,7 +207,7 @@ size_t obs_partials_len(int n, int num_sms) {
 cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, const ClauseLP* cl) {
   const long long ntiles = n > kLowBits ? (1ll << (n - kLowBits)) : 1ll;
   const size_t smem = 16u * static_cast<size_t>(m) + static_cast<size_t>(kObsWarps) * 8u * (m + 16);
-  cudaError_t err = cudaFuncSetAttribute(diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaError_t err = allow_smem(reinterpret_cast<const void*>(diag_kernel), 16u * QAA_MAX_CLAUSES_DEV + static_cast<size_t>(kObsWarps) * 8u * (QAA_MAX_CLAUSES_DEV + 16));
   if (err != cudaSuccess) return err;
   long long grid = (ntiles + kObsWarps - 1) / kObsWarps;
   if (grid > 4ll * lc.num_sms) grid = 4ll * lc.num_sms;
@@ -220,7 +220,7 @@ cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, in
   const int P = obs_grid(lc.num_sms);
   const long long ntiles = n > kLowBits ? (1ll << (n - kLowBits)) : 1ll;
   const size_t smem = obs_low_smem(m);
-  cudaError_t err = cudaFuncSetAttribute(obs_low_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaError_t err = allow_smem(reinterpret_cast<const void*>(obs_low_kernel), obs_low_smem(QAA_MAX_CLAUSES_DEV));
   if (err != cudaSuccess) return err;
   obs_low_kernel<<<P, kObsWarps * 32, smem, lc.stream>>>(psi, n, m, cl, ntiles, partials);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -100,17 +100,20 @@ struct OnchipLayout {
 
 size_t onchip_smem_bytes(int n, int m) { return OnchipLayout(n, m).total; }
 
-__global__ void __launch_bounds__(kOnchipThreads)
-    onchip_kernel(float2* __restrict__ psi, int n, int m, const ClauseMV* __restrict__ cl,
-                  const float2* __restrict__ ptab, const float2* __restrict__ btab, int nsteps, int first_p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// One whole run (or chunk of a run) of one instance, by one CTA.
+__device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseMV* __restrict__ cl,
+                           const float2* __restrict__ ptab, const float2* __restrict__ btab, int nsteps, int first_p,
+                           unsigned char* smem, bool init_uniform = false, float init_val = 0.0f) {
   const int N = 1 << n;
   const OnchipLayout L(n, m);
   float2* s_psi = reinterpret_cast<float2*>(smem);
   uint16_t* s_e = reinterpret_cast<uint16_t*>(smem + L.off_e);
   ClauseMV* s_cl = reinterpret_cast<ClauseMV*>(smem + L.off_cl);
   for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
-  for (int x = threadIdx.x; x < N; x += blockDim.x) s_psi[oswz(x)] = psi[x];
+  // the uniform start state 2^(-n/2) (Sec. 2.1, value rounded on the host as
+  // for qaa_init_uniform), or the caller's state
+  const float2 u = make_float2(init_val, 0.0f);
+  for (int x = threadIdx.x; x < N; x += blockDim.x) s_psi[oswz(x)] = init_uniform ? u : psi[x];
   __syncthreads();
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     int e = 0;
@@ -146,11 +149,35 @@ __global__ void __launch_bounds__(kOnchipThreads)
   for (int x = threadIdx.x; x < N; x += blockDim.x) psi[x] = s_psi[oswz(x)];
 }
 
+__global__ void __launch_bounds__(kOnchipThreads)
+    onchip_kernel(float2* __restrict__ psi, int n, int m, const ClauseMV* __restrict__ cl,
+                  const float2* __restrict__ ptab, const float2* __restrict__ btab, int nsteps, int first_p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  onchip_run(psi, n, m, cl, ptab, btab, nsteps, first_p, smem);
+}
+
+// A batch of independent instances of uneven size and length: one CTA each.
+__global__ void __launch_bounds__(kOnchipThreads) onchip_batch_kernel(const OnchipJob* __restrict__ jobs, int njobs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (static_cast<int>(blockIdx.x) >= njobs) return;
+  const OnchipJob jb = jobs[blockIdx.x];
+  onchip_run(jb.psi, jb.n, jb.m, jb.cl, jb.ptab, jb.btab, jb.nsteps, jb.first_p, smem, jb.init != 0, jb.init_val);
+}
+
+cudaError_t launch_onchip_batch(const LaunchCtx& lc, const OnchipJob* jobs_dev, int njobs, size_t smem_bytes) {
+  if (njobs <= 0) return cudaSuccess;
+  cudaError_t err =
+      allow_smem(reinterpret_cast<const void*>(onchip_batch_kernel), onchip_smem_bytes(kOnchipMaxBits, QAA_MAX_CLAUSES_DEV));
+  if (err != cudaSuccess) return err;
+  onchip_batch_kernel<<<njobs, kOnchipThreads, smem_bytes, lc.stream>>>(jobs_dev, njobs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_onchip(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseMV* cl, const float2* ptab,
                           const float2* btab, int nsteps, bool first_p) {
   if (n > kOnchipMaxBits) return cudaErrorInvalidValue;
   const size_t smem = onchip_smem_bytes(n, m);
-  cudaError_t err = cudaFuncSetAttribute(onchip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaError_t err = allow_smem(reinterpret_cast<const void*>(onchip_kernel), onchip_smem_bytes(kOnchipMaxBits, QAA_MAX_CLAUSES_DEV));
   if (err != cudaSuccess) return err;
   onchip_kernel<<<1, kOnchipThreads, smem, lc.stream>>>(psi, n, m, cl, ptab, btab, nsteps, first_p ? 1 : 0);
   return cudaGetLastError();

@@ -271,7 +271,7 @@ static cudaError_t launch_sp(const LaunchCtx& lc, float2* psi, int n, int a, boo
   const long long ntiles = 1ll << (n - Q - C);
   const size_t smem = static_cast<size_t>(G::SLOTS) * 8u + static_cast<size_t>(n + 1) * 8u;
   auto kern = wbw ? sp_kernel<Q, C, true> : sp_kernel<Q, C, false>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaError_t err = allow_smem(reinterpret_cast<const void*>(kern), static_cast<size_t>(G::SLOTS) * 8u + 64u * 8u);
   if (err != cudaSuccess) return err;
   int occ = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, G::NT, smem);
@@ -288,7 +288,7 @@ static cudaError_t launch_lp(const LaunchCtx& lc, float2* psi, int n, int m, con
   const long long ntiles = 1ll << (n - kLowBits);
   const size_t smem = lp_smem_bytes(m);
   auto kern = lp_kernel<KIND>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaError_t err = allow_smem(reinterpret_cast<const void*>(kern), lp_smem_bytes(QAA_MAX_CLAUSES_DEV));
   if (err != cudaSuccess) return err;
   int occ = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLpWarps * 32, smem);

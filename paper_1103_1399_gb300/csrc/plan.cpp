@@ -1,0 +1,198 @@
+// Clause encoding and pass planning shared by the handle API and the server.
+//
+// Pass plan for n >= 15 (state streamed from HBM): G1 = bits 0..9 (low pass),
+// the remaining n-10 bits in 1..3 strided groups of 5..10 bits.  The popcount
+// phase B needs every qubit in the Hadamard basis, so it is fused into the pass
+// of whichever strided group is transformed last (the phase group); the others
+// are transformed before it (ascending) and after it (descending).  Per Strang
+// step: phase group W B W, the other groups down, the low pass W P W (merging
+// the half phases of two steps), the other groups up: 2g-2 HBM round trips for
+// g groups.  n <= 14 runs entirely on chip.
+#include <cstdlib>
+#include <mutex>
+#include <set>
+#include <utility>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine_internal.h"
+#include "qaa.h"
+
+namespace qaa {
+
+int encode_clauses(int n, const int32_t* lits, int m, std::vector<ClauseMV>& mv, std::vector<ClauseLP>& lp,
+                   std::string& err) {
+  mv.resize(static_cast<size_t>(m));
+  lp.resize(static_cast<size_t>(m));
+  for (int c = 0; c < m; ++c) {
+    unsigned long long mask = 0, viol = 0;
+    int width = 0;
+    for (int k = 0; k < 3; ++k) {
+      const int32_t lit = lits[3 * c + k];
+      if (lit == 0) continue;
+      const long long a = lit < 0 ? -static_cast<long long>(lit) : lit;
+      if (a > n) {
+        err = "clause " + std::to_string(c) + ": literal beyond n";
+        return QAA_E_ARG;
+      }
+      const unsigned long long bit = 1ull << (a - 1);
+      if (mask & bit) {
+        err = "clause " + std::to_string(c) + ": variable repeated in a clause";
+        return QAA_E_ARG;
+      }
+      mask |= bit;
+      if (lit < 0) viol |= bit;
+      ++width;
+    }
+    if (width == 0) {
+      err = "clause " + std::to_string(c) + ": no literals";
+      return QAA_E_ARG;
+    }
+    mv[c] = {mask, viol};
+    ClauseLP e;
+    e.hi_mask = static_cast<unsigned>(mask >> kLowBits);
+    e.hi_viol = static_cast<unsigned>(viol >> kLowBits);
+    unsigned p0 = 0, p5 = 0;
+    const unsigned m0 = static_cast<unsigned>(mask & 31u), v0 = static_cast<unsigned>(viol & 31u);
+    const unsigned m5 = static_cast<unsigned>((mask >> 5) & 31u), v5 = static_cast<unsigned>((viol >> 5) & 31u);
+    for (unsigned j = 0; j < 32; ++j) {
+      if ((j & m0) == v0) p0 |= 1u << j;
+      if ((j & m5) == v5) p5 |= 1u << j;
+    }
+    e.pat0 = p0;
+    e.pat5 = p5;
+    lp[c] = e;
+  }
+  return QAA_OK;
+}
+
+void make_plan(int n, PassPlan& plan) {
+  plan = PassPlan();
+  plan.n = n;
+  plan.onchip = n <= kOnchipMaxBits;
+  const char* env = std::getenv("QAA_PASSES");
+  plan.use_tma = tma_available() && !(env && std::strcmp(env, "classic") == 0);
+  if (plan.onchip) return;
+  const int rest = n - kLowBits;
+  std::vector<int> sizes;
+  if (const char* gb = std::getenv("QAA_GROUP_BITS")) {
+    int sum = 0;
+    bool ok = true;
+    for (const char* p = gb; *p;) {
+      const int q = std::atoi(p);
+      if (q < 5 || q > 10) ok = false;
+      sizes.push_back(q);
+      sum += q;
+      while (*p && *p != ',') ++p;
+      if (*p == ',') ++p;
+    }
+    if (!ok || sum != rest) sizes.clear();
+  }
+  if (sizes.empty()) {
+    const int ng = (rest + 9) / 10;
+    const int base = rest / ng, extra = rest % ng;
+    for (int g = 0; g < ng; ++g) sizes.push_back(base + (g < extra ? 1 : 0));
+  }
+  int a = kLowBits;
+  for (int q : sizes) {
+    plan.strided.push_back({a, q, a + 5});
+    a += q;
+  }
+  // Two 10-bit strided groups [10,20) and [20,30): recombine them as
+  // {10..14, 25..29} and {15..24}.  With [20,30) as one group every tile has
+  // 1024 rows 8 MiB apart, each on its own memory page; recombined, a tile
+  // spans at most 128 pages (measured: 6.7 ms -> 3.1 ms per pass at n = 30).
+  const char* sg = std::getenv("QAA_SPLIT_GROUPS");
+  const bool split = plan.use_tma && !(sg && std::atoi(sg) == 0);
+  if (split && plan.strided.size() == 2 && plan.strided[0].q == 10 && plan.strided[1].q == 10) {
+    plan.strided[0] = {kLowBits, 10, kLowBits + 15};
+    plan.strided[1] = {kLowBits + 5, 10, kLowBits + 10};
+  }
+  const int ng = static_cast<int>(plan.strided.size());
+  plan.phase_group = ng - 1;
+  if (const char* pg = std::getenv("QAA_PHASE_GROUP")) {
+    const int v = std::atoi(pg);
+    if (v >= 0 && v < ng) plan.phase_group = v;
+  }
+  // Contiguous run per tile row: 128 bytes for the plain strided passes, 64
+  // bytes (three CTAs per SM) for the heavier pass that hosts the phase.
+  const char* rg = std::getenv("QAA_RUN128_GROUPS");
+  const int rmask = rg ? std::atoi(rg) : -1;
+  plan.run_c.resize(static_cast<size_t>(ng));
+  for (int i = 0; i < ng; ++i)
+    plan.run_c[i] = rmask >= 0 ? (((rmask >> i) & 1) ? 4 : 0) : (i == plan.phase_group ? 0 : 4);
+}
+
+void build_passes(const PassPlan& plan, long long k0, long long k1, long long c0, long long c1,
+                  std::vector<Pass>& out) {
+  out.clear();
+  const int ng = static_cast<int>(plan.strided.size());
+  const int pg = plan.phase_group;
+  const Group top = plan.strided[pg];
+  auto other = [&](int i) {
+    const Group& g = plan.strided[i];
+    out.push_back({kSpW, g.a, g.q, 0, plan.run_c[i], 0, g.a2});
+  };
+  auto up = [&]() {
+    for (int i = 0; i < ng; ++i)
+      if (i != pg) other(i);
+  };
+  auto down = [&]() {
+    for (int i = ng - 1; i >= 0; --i)
+      if (i != pg) other(i);
+  };
+  if (c0 == k0) {
+    out.push_back({kLpFirst, 0, 0, 0, 0, 0, 0});
+    up();
+  }
+  for (long long k = c0; k < c1; ++k) {
+    out.push_back({kSpWBW, top.a, top.q, 0, plan.run_c[pg], static_cast<int>(k - c0), top.a2});
+    down();
+    if (k == k1 - 1) {
+      out.push_back({kLpLast, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0});
+    } else {
+      out.push_back({kLpMerge, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0});
+      up();
+    }
+  }
+}
+
+std::string describe_plan(const PassPlan& plan) {
+  if (plan.onchip) return "on-chip: whole run in one CTA's shared memory (n=" + std::to_string(plan.n) + ")";
+  const int ng = static_cast<int>(plan.strided.size());
+  const char* wk = plan.wht_kind == 1 ? "tensor-core BF16x3" : (plan.wht_kind == 2 ? "tensor-core BF16x2" : "FP32");
+  std::string d = "streaming, " + std::string(plan.wht_kind ? "plain" : (plan.use_tma ? "TMA" : "classic")) +
+                  " loads, " + wk + " WHT; low pass bits [0,10) W.P.W";
+  for (int i = 0; i < ng; ++i) {
+    const Group& g = plan.strided[i];
+    d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";
+    if (g.q > 5) d += "+[" + std::to_string(g.a2) + "," + std::to_string(g.a2 + g.q - 5) + ")";
+    d += i == plan.phase_group ? " W.B.W" : " W";
+    if (plan.use_tma && !plan.wht_kind) d += plan.run_c[i] == 4 ? " 128B runs" : " 64B runs";
+  }
+  d += "; " + std::to_string(2 * ng) + " HBM round trips per step";
+  return d;
+}
+
+cudaError_t allow_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, func})) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e == cudaSuccess) done.insert({dev, func});
+  return e;
+}
+
+cudaError_t launch_planned_pass(const LaunchCtx& lc, const PassPlan& plan, const Pass& p, float2* psi, int m,
+                                const ClauseLP* cl, const float2* ptab, const float2* btab, int* err) {
+  if (plan.wht_kind) return launch_pass_tc(lc, p, psi, plan.n, m, cl, ptab, btab, plan.wht_kind == 1 ? 3 : 2);
+  if (plan.use_tma) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err);
+  return launch_pass(lc, p, psi, plan.n, m, cl, ptab, btab);
+}
+
+}  // namespace qaa

@@ -40,6 +40,7 @@ constexpr int kLowTile = 1 << kLowBits;
 
 // In-register bit-sliced counters hold up to 10 bits (QAA_MAX_CLAUSES = 1023).
 constexpr int kPlanes = 10;
+constexpr int QAA_MAX_CLAUSES_DEV = 1023;
 
 // ---- pass descriptors -------------------------------------------------------
 enum PassKind : int {
@@ -80,6 +81,18 @@ constexpr int kOnchipMaxBits = 14;
 cudaError_t launch_onchip(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseMV* cl,
                           const float2* ptab, const float2* btab, int nsteps, bool first_p);
 size_t onchip_smem_bytes(int n, int m);
+// Batched on-chip evolution: one CTA per job, dynamic shared memory = the
+// largest onchip_smem_bytes of the batch.  jobs_dev is a device array.
+struct OnchipJob {
+  float2* psi;
+  const ClauseMV* cl;
+  const float2* ptab;
+  const float2* btab;
+  int n, m, nsteps, first_p;
+  int init;        // nonzero: start from the uniform superposition instead of reading psi
+  float init_val;  // that amplitude, 2^(-n/2) rounded to FP32 on the host
+};
+cudaError_t launch_onchip_batch(const LaunchCtx& lc, const OnchipJob* jobs_dev, int njobs, size_t smem_bytes);
 cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, const ClauseLP* cl);
 // Observables: partials has room for obs_partials_len(n) doubles; result is 5 doubles
 // {norm, <H_P>, ground_prob, ground_count, sum of pair correlations} on the device.
@@ -99,6 +112,24 @@ cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int
 // hi + mid + lo, parts = 2: hi + lo) with FP32 accumulation.
 cudaError_t launch_pass_tc(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
                            const float2* ptab, const float2* btab, int parts);
+
+// Persistent evolution of one instance with 15 <= n <= 24 in one cooperative
+// launch (persist.cu): every pass of every step inside the kernel, separated by
+// a bounded grid barrier (bar: two zeroed words).  Tables for the whole run
+// (K + 1 P rows, K B rows).  Contiguous strided groups only.
+constexpr int kPersistMaxBits = 24;
+struct PersistPlan {
+  int ng, phase_group;
+  int ga[3], gq[3];
+};
+cudaError_t launch_persist(const LaunchCtx& lc, const PersistPlan& pp, float2* psi, int n, int m, const ClauseLP* cl,
+                           const float2* ptab, const float2* btab, int K, unsigned* bar, int* err, int grid);
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` (its worst case over
+// every instance the library accepts) once per device.  Launches then request
+// only what they need; a per-launch limit would race between threads that
+// launch the same kernel with different sizes.
+cudaError_t allow_smem(const void* func, size_t bytes);
 
 // Store a message for qaa_last_error() on the calling thread.
 void set_last_error(const std::string& msg);

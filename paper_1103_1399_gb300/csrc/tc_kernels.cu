@@ -323,7 +323,9 @@ static cudaError_t launch_lp_tc(const LaunchCtx& lc, float2* psi, int n, int m, 
   const long long ntiles = 1ll << (n - kLowBits);
   const size_t smem = 16u * m + ((8u * (m + 1) + 15u) & ~15u) + static_cast<size_t>(kTcWarps) * (8u * kLowTile + 8u * (m + 16));
   auto kern = lp_tc_kernel<KIND, PARTS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  const size_t worst = 16u * QAA_MAX_CLAUSES_DEV + ((8u * (QAA_MAX_CLAUSES_DEV + 1) + 15u) & ~15u) +
+                       static_cast<size_t>(kTcWarps) * (8u * kLowTile + 8u * (QAA_MAX_CLAUSES_DEV + 16));
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), worst);
   if (e != cudaSuccess) return e;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcWarps * 32, smem);
@@ -343,7 +345,7 @@ static cudaError_t launch_sp_tc(const LaunchCtx& lc, float2* psi, int n, int a1,
   const long long ntiles = 1ll << (n - Q - C);
   const size_t smem = static_cast<size_t>(G::TILE) * 8u + 64u * 8u;
   auto kern = wbw ? sp_tc_kernel<Q, C, true, PARTS> : sp_tc_kernel<Q, C, false, PARTS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, G::NT, smem);

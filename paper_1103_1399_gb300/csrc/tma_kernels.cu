@@ -346,19 +346,18 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+static EncodeTiledFn lookup_encode() {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return reinterpret_cast<EncodeTiledFn>(p);
+  cudaGetLastError();
+  return nullptr;
+}
+
 static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-    else
-      cudaGetLastError();
-  }
+  static const EncodeTiledFn fn = lookup_encode();  // initialised once, thread safe
   return fn;
 }
 
@@ -385,7 +384,7 @@ static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int 
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const long long ntiles = 1ll << (n - Q - C);
   auto kern = wbw ? sp_tma_kernel<Q, C, true> : sp_tma_kernel<Q, C, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(G::smem));
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), G::smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, G::NT, G::smem);
@@ -414,7 +413,7 @@ static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m,
   const long long ntiles = 1ll << (n - kLowBits);
   const LpTmaLayout L(m);
   auto kern = lp_tma_kernel<KIND>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.total));
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), LpTmaLayout(QAA_MAX_CLAUSES_DEV).total);
   if (e != cudaSuccess) return e;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLpTmaWarps * 32, L.total);
