@@ -100,6 +100,57 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream);
  */
 int qaa_set_variant(qaa_handle h, int wht_kind, int q);
 
+/*
+ * qaa_set_launch_mode -- how qaa_evolve* issue the streaming passes (n >= 15;
+ * the on-chip path for n <= 14 is one launch per chunk either way).
+ *   QAA_LAUNCH_PASSES (0, default): one kernel launch per pass from the host.
+ *   QAA_LAUNCH_GRAPH  (1): one CUDA graph per step range, launched once: a
+ *     WHILE conditional node whose body is 8 Strang steps, the phase rows of
+ *     each iteration computed on the device from the same FP64 formulas, so
+ *     the result is the same bit for bit.  The graph is kept and relaunched
+ *     while psi, T, steps, the range, the schedule pointer, the variant and the
+ *     stream stay the same; any change rebuilds it (a stream synchronisation
+ *     and a few hundred microseconds of host time).  The handle allocates a
+ *     small device scratch (the loop counter and 8 steps of phase rows) on the
+ *     first graph launch.  The integrator is the paper's Eq. (1) Hamiltonian
+ *     split as in qaa_evolve; the paper has no launch-graph counterpart.
+ * Returns QAA_E_ARG for an unknown mode.
+ */
+/*
+ * qaa_autotune -- choose the pass plan of a streaming-size handle (n >= 15)
+ * by timing candidates on the GPU.  Round 1 times the default plan and every
+ * split of bits 10..n-1 into the fewest strided groups of 5..10 bits (qubits
+ * per pass) with every choice of the group that hosts the popcount phase;
+ * round 2 toggles the contiguous run per tile row (64 or 128 bytes) of each
+ * group of >= 7 bits; round 3 tries recombining two 10-bit groups; round 4
+ * plain loads instead of TMA.  Each candidate is timed with CUDA events as the
+ * best of two runs of `steps` Strang steps (1..64) after one untimed run.
+ * Rounds stop once budget_ms of host time is spent (<= 0: 60 s); round 1's
+ * first candidate always runs.
+ *   psi      device complex64[2^n], 16-byte aligned: scratch, overwritten
+ *            (re-initialise it afterwards).
+ *   report   optional (NULL allowed): one line per timed candidate, then the
+ *            choice; truncated to len - 1 bytes.
+ * The fastest plan becomes this handle's plan and is recorded for n on the
+ * current device: every later qaa_create and server request with the same n
+ * in this process uses it (unless a QAA_* plan override is set in the
+ * environment).  Results of different plans agree within FP32 rounding (the
+ * butterfly order differs).  Synchronous.  For n <= 14 there is nothing to
+ * tune (QAA_OK, report says so).  The paper has no counterpart.
+ */
+int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* report, size_t len);
+
+/* Number of round-1 autotune candidates for n (0 for n <= 14), with their
+ * descriptions one per line in buf (NULL allowed).  Needs no GPU. */
+int qaa_tune_candidates(int n, char* buf, size_t len);
+
+/* Forget every plan recorded by qaa_autotune in this process. */
+int qaa_forget_tuned_plans(void);
+
+#define QAA_LAUNCH_PASSES 0
+#define QAA_LAUNCH_GRAPH 1
+int qaa_set_launch_mode(qaa_handle h, int mode);
+
 /* psi[x] = 2^(-n/2) for all x: the ground state of H_B (Sec. 2.1).  Asynchronous. */
 int qaa_init_uniform(qaa_handle h, void* psi);
 
@@ -277,7 +328,8 @@ typedef enum {
   QAA_K_OBSERVE = 7,       /* observable reductions (all kernels of a call) */
   QAA_K_DIAG = 8,          /* E(x) export                                   */
   QAA_K_INIT = 9,          /* uniform-state initialisation                  */
-  QAA_K_COUNT = 10
+  QAA_K_GRAPH = 10,        /* one launch-graph evolve (all its passes)      */
+  QAA_K_COUNT = 11
 } qaa_kernel_kind;
 
 int qaa_profile_enable(qaa_handle h, int on);

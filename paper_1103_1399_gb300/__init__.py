@@ -7,7 +7,8 @@ imports without the library.
 """
 
 _EXPORTS = ("Instance", "QaaError", "lib", "flatten_clauses", "SIGNATURES", "MAX_QUBITS", "MAX_CLAUSES",
-            "LIB_PATH", "Obs", "KERNEL_KINDS", "Server")
+            "LIB_PATH", "Obs", "KERNEL_KINDS", "Server", "tune_candidates", "forget_tuned_plans",
+            "LAUNCH_PASSES", "LAUNCH_GRAPH")
 
 __all__ = list(_EXPORTS)
 

@@ -54,6 +54,10 @@ SIGNATURES = {
     "qaa_destroy": (_c_int, [_vp]),
     "qaa_set_stream": (_c_int, [_vp, _vp]),
     "qaa_set_variant": (_c_int, [_vp, _c_int, _c_int]),
+    "qaa_set_launch_mode": (_c_int, [_vp, _c_int]),
+    "qaa_autotune": (_c_int, [_vp, _vp, _c_int, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
+    "qaa_tune_candidates": (_c_int, [_c_int, ctypes.c_char_p, ctypes.c_size_t]),
+    "qaa_forget_tuned_plans": (_c_int, []),
     "qaa_init_uniform": (_c_int, [_vp, _vp]),
     "qaa_evolve": (_c_int, [_vp, _vp, _dbl, _i64]),
     "qaa_evolve_range": (_c_int, [_vp, _vp, _dbl, _i64, _i64, _i64]),
@@ -78,7 +82,8 @@ SIGNATURES = {
 }
 
 KERNEL_KINDS = ["low_first", "low_merge", "low_last", "strided", "strided_phase", "tables", "onchip",
-                "observe", "diag", "init"]
+                "observe", "diag", "init", "graph"]
+LAUNCH_PASSES, LAUNCH_GRAPH = 0, 1
 
 
 def _load():
@@ -110,6 +115,20 @@ def _ptr(x):
     if hasattr(x, "data_ptr"):
         return x.data_ptr()
     raise TypeError("expected a device pointer (int) or an object with data_ptr()")
+
+
+def tune_candidates(n):
+    """Round-1 autotune candidates for n, as plan descriptions (qaa_tune_candidates; no GPU needed)."""
+    buf = ctypes.create_string_buffer(1 << 20)
+    count = lib.qaa_tune_candidates(int(n), buf, len(buf))
+    if count < 0:
+        _check(count)
+    return [line for line in buf.value.decode().split("\n") if line][:count]
+
+
+def forget_tuned_plans():
+    """Drop every plan recorded by autotune in this process (qaa_forget_tuned_plans)."""
+    _check(lib.qaa_forget_tuned_plans())
 
 
 def _check_state(inst, psi):
@@ -174,6 +193,19 @@ class Instance:
 
     def set_variant(self, wht_kind=0, q=0):
         _check(lib.qaa_set_variant(self._h, int(wht_kind), int(q)))
+
+    def autotune(self, psi, steps=3, budget_ms=60000.0):
+        """Time candidate pass plans on psi (overwritten); keep the fastest for this
+        handle and for later handles / server requests with the same n.  Returns the
+        report text (qaa_autotune)."""
+        _check_state(self, psi)
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(lib.qaa_autotune(self._h, _ptr(psi), int(steps), float(budget_ms), buf, len(buf)))
+        return buf.value.decode()
+
+    def set_launch_mode(self, mode):
+        """0: one launch per pass; 1: one CUDA graph per evolve range (qaa_set_launch_mode)."""
+        _check(lib.qaa_set_launch_mode(self._h, int(mode)))
 
     def init_uniform(self, psi):
         _check_state(self, psi)

@@ -2,7 +2,9 @@
 // scheduling in chunks of steps, kernel launch order (the pass plan comes from
 // plan.cpp), observables and launch profiling.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -51,6 +53,22 @@ struct qaa_ctx {
   double* h_res = nullptr;  // pinned
   int* d_err = nullptr;     // set by kernels whose bounded waits expired
   qaa::PassPlan plan;
+  // launch graphs (QAA_LAUNCH_GRAPH): the last built graph and what it was built for
+  int launch_mode = QAA_LAUNCH_PASSES;
+  void* d_gscratch = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  struct GraphKey {
+    const void* psi;
+    double dt;
+    const double* s_dev;
+    long long K, k0, k1;
+    int wht_kind;
+    cudaStream_t stream;
+    bool operator==(const GraphKey& o) const {
+      return psi == o.psi && std::memcmp(&dt, &o.dt, sizeof dt) == 0 && s_dev == o.s_dev && K == o.K && k0 == o.k0 &&
+             k1 == o.k1 && wht_kind == o.wht_kind && stream == o.stream;
+    }
+  } gkey{};
   // launch profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
@@ -149,6 +167,43 @@ int check_device_error(qaa_ctx* h) {
   return QAA_OK;
 }
 
+// Streaming plan, launch-graph mode: build (or reuse) the graph of the whole
+// range and launch it.  The graph is rebuilt when psi, the schedule, the range,
+// the variant or the stream changes.
+int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, long long k1, const double* s_dev) {
+  if (!h->d_gscratch) {
+    if (cudaMalloc(&h->d_gscratch, qaa::graph_scratch_bytes(h->n, h->m)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QAA_E_NOMEM, "cannot allocate graph scratch");
+    }
+  }
+  const qaa_ctx::GraphKey key{psi, dt, s_dev, K, k0, k1, h->plan.wht_kind, h->stream};
+  if (!h->gexec || !(key == h->gkey)) {
+    if (h->gexec) {
+      QAA_CK(cudaStreamSynchronize(h->stream));
+      QAA_CK(cudaGraphExecDestroy(h->gexec));
+      h->gexec = nullptr;
+    }
+    qaa::GraphSpec gs;
+    gs.plan = &h->plan;
+    gs.psi = psi;
+    gs.m = h->m;
+    gs.cl = h->d_lp;
+    gs.err = h->d_err;
+    gs.dt = dt;
+    gs.s_dev = s_dev;
+    gs.K = K;
+    gs.k0 = k0;
+    gs.k1 = k1;
+    gs.num_sms = h->num_sms;
+    qaa::graph_scratch_split(h->d_gscratch, h->m, gs);
+    QAA_CK(qaa::build_evolve_graph(gs, &h->gexec));
+    h->gkey = key;
+  }
+  QAA_CK(timed(h, QAA_K_GRAPH, [&] { return cudaGraphLaunch(h->gexec, h->stream); }));
+  return QAA_OK;
+}
+
 int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, long long k1, const double* s_host) {
   int st = check_handle(h);
   if (st) return st;
@@ -176,6 +231,8 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
     QAA_CK(cudaMemcpyAsync(h->d_s, s_host, need * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     s_dev = h->d_s;
   }
+  if (h->launch_mode == QAA_LAUNCH_GRAPH && h->n > qaa::kOnchipMaxBits)
+    return evolve_graph(h, static_cast<float2*>(psi), dt, K, k0, k1, s_dev);
   const long long chunk = std::min(kChunkSteps, k1 - k0);
   const size_t prow = static_cast<size_t>(h->m + 1), brow = static_cast<size_t>(h->n + 1);
   st = ensure_tab(h, static_cast<size_t>(chunk + 1) * prow + static_cast<size_t>(chunk) * brow);
@@ -296,6 +353,8 @@ int qaa_destroy(qaa_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   cudaFree(h->d_mv);
   cudaFree(h->d_lp);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  cudaFree(h->d_gscratch);
   cudaFree(h->d_tab);
   cudaFree(h->d_s);
   cudaFree(h->d_part);
@@ -322,6 +381,168 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (wht_kind < 0 || wht_kind > 2) return fail(QAA_E_ARG, "unknown wht_kind (0 = FP32, 1 = BF16x3, 2 = BF16x2)");
   if (q != 0) return fail(QAA_E_ARG, "only automatic qubits-per-pass (q = 0) is available");
   h->plan.wht_kind = wht_kind;
+  return QAA_OK;
+}
+
+namespace {
+
+// One timing of `plan` on the handle: init, `steps` Strang steps (dt = 0.1),
+// the best of two runs, in ms per step; < 0 on a launch error.
+double time_plan(qaa_ctx* h, float2* psi, const qaa::PassPlan& plan, int steps) {
+  const int kind = h->plan.wht_kind;
+  h->plan = plan;
+  h->plan.wht_kind = kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    if (a) cudaEventDestroy(a);
+    return -1.0;
+  }
+  double best = -1.0;
+  for (int rep = 0; rep < 3; ++rep) {
+    if (qaa::launch_init_uniform(lctx(h), psi, h->n) != cudaSuccess) break;
+    if (rep > 0) cudaEventRecord(a, h->stream);
+    if (evolve_impl(h, psi, 0.1 * steps, steps, 0, steps, nullptr) != QAA_OK) break;
+    if (rep > 0) {
+      cudaEventRecord(b, h->stream);
+      if (cudaEventSynchronize(b) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      const double per = ms / steps;
+      if (best < 0 || per < best) best = per;
+    }
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess || check_device_error(h) != QAA_OK) best = -1.0;
+  cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+}  // namespace
+
+int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* report, size_t len) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (!psi) return fail(QAA_E_ARG, "psi is null");
+  if (reinterpret_cast<uintptr_t>(psi) % 16u) return fail(QAA_E_ARG, "psi must be 16-byte aligned");
+  if (steps < 1 || steps > 64) return fail(QAA_E_ARG, "steps must be in [1, 64]");
+  std::string rep;
+  auto finish = [&](int code) {
+    if (report && len > 0) {
+      std::strncpy(report, rep.c_str(), len - 1);
+      report[len - 1] = '\0';
+    }
+    return code;
+  };
+  if (h->n <= qaa::kOnchipMaxBits) {
+    rep = "on-chip evolver: no pass plan to tune\n";
+    return finish(QAA_OK);
+  }
+  if (!(budget_ms > 0)) budget_ms = 60000.0;
+  const bool prof = h->prof;
+  const int mode = h->launch_mode;
+  h->prof = false;
+  h->launch_mode = QAA_LAUNCH_PASSES;
+  float2* p = static_cast<float2*>(psi);
+  const auto t0 = std::chrono::steady_clock::now();
+  auto spent = [&] {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  };
+  qaa::PassPlan best;
+  double best_ms = -1.0;
+  auto consider = [&](const qaa::PassPlan& cand) {
+    const double ms = time_plan(h, p, cand, steps);
+    char line[64];
+    std::snprintf(line, sizeof line, "%10.4f ms/step  ", ms);
+    rep += std::string(line) + qaa::describe_plan(cand) + "\n";
+    if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = cand;
+    }
+  };
+  // round 1: group widths and the phase group
+  std::vector<qaa::PassPlan> cands;
+  qaa::plan_candidates(h->n, cands);
+  for (const auto& c : cands) {
+    if (best_ms > 0 && spent() > budget_ms) break;
+    consider(c);
+  }
+  if (best_ms < 0) {
+    h->prof = prof;
+    h->launch_mode = mode;
+    qaa::make_plan(h->n, h->plan);
+    return finish(fail(QAA_E_CUDA, "autotune: no candidate plan ran"));
+  }
+  // round 2: run length of each group that has a choice (Q >= 7 on TMA passes)
+  if (best.use_tma)
+    for (size_t i = 0; i < best.strided.size() && spent() <= budget_ms; ++i) {
+      if (best.strided[i].q < 7) continue;
+      qaa::PassPlan c = best;
+      c.run_c[i] = c.run_c[i] == 4 ? 0 : 4;
+      consider(c);
+    }
+  // round 3: two 10-bit groups recombined as {10..14, 25..29} and {15..24}
+  if (best.use_tma && best.strided.size() == 2 && best.strided[0].q == 10 && best.strided[1].q == 10 &&
+      spent() <= budget_ms) {
+    qaa::PassPlan c = best;
+    const bool split = c.strided[0].a2 != c.strided[0].a + 5;
+    if (split) {
+      c.strided[0] = {qaa::kLowBits, 10, qaa::kLowBits + 5};
+      c.strided[1] = {qaa::kLowBits + 10, 10, qaa::kLowBits + 15};
+    } else {
+      c.strided[0] = {qaa::kLowBits, 10, qaa::kLowBits + 15};
+      c.strided[1] = {qaa::kLowBits + 5, 10, qaa::kLowBits + 10};
+    }
+    consider(c);
+  }
+  // round 4: plain loads instead of TMA
+  if (best.use_tma && spent() <= budget_ms) {
+    qaa::PassPlan c = best;
+    c.use_tma = false;
+    if (c.strided.size() == 2 && c.strided[0].a2 != c.strided[0].a + 5) {  // plain loads need contiguous groups
+      c.strided[0] = {qaa::kLowBits, 10, qaa::kLowBits + 5};
+      c.strided[1] = {qaa::kLowBits + 10, 10, qaa::kLowBits + 15};
+    }
+    consider(c);
+  }
+  const int kind = h->plan.wht_kind;
+  h->plan = best;
+  h->plan.wht_kind = kind;
+  qaa::PassPlan rec = best;
+  rec.wht_kind = 0;
+  qaa::set_tuned_plan(rec);
+  h->prof = prof;
+  h->launch_mode = mode;
+  char line[96];
+  std::snprintf(line, sizeof line, "chosen (%.4f ms/step, %.0f ms spent): ", best_ms, spent());
+  rep += std::string(line) + qaa::describe_plan(best) + "\n";
+  return finish(QAA_OK);
+}
+
+int qaa_tune_candidates(int n, char* buf, size_t len) {
+  if (n < 1 || n > QAA_MAX_QUBITS) return fail(QAA_E_ARG, "n out of range [1, 34]");
+  std::vector<qaa::PassPlan> cands;
+  qaa::plan_candidates(n, cands);
+  std::string d;
+  for (const auto& c : cands) d += qaa::describe_plan(c) + "\n";
+  if (buf && len > 0) {
+    std::strncpy(buf, d.c_str(), len - 1);
+    buf[len - 1] = '\0';
+  }
+  return static_cast<int>(cands.size());
+}
+
+int qaa_forget_tuned_plans(void) {
+  qaa::clear_tuned_plans();
+  return QAA_OK;
+}
+
+int qaa_set_launch_mode(qaa_handle h, int mode) {
+  if (!h) return fail(QAA_E_ARG, "null handle");
+  if (mode != QAA_LAUNCH_PASSES && mode != QAA_LAUNCH_GRAPH)
+    return fail(QAA_E_ARG, "unknown launch mode (0 = per-pass launches, 1 = launch graph)");
+  h->launch_mode = mode;
   return QAA_OK;
 }
 

@@ -31,10 +31,24 @@ struct PassPlan {
   std::vector<int> run_c;      // per strided group: 4 = 128-byte runs, 0 = default
 };
 
+// Plan for n: the one qaa_autotune chose for n on the current device, if any
+// and if no tuning override is set in the environment; otherwise the default.
+void make_plan(int n, PassPlan& plan);
 // Default plan for n, with the tuning overrides QAA_PASSES, QAA_SPLIT_GROUPS,
 // QAA_PHASE_GROUP, QAA_RUN128_GROUPS and QAA_GROUP_BITS read from the
 // environment.
-void make_plan(int n, PassPlan& plan);
+void make_default_plan(int n, PassPlan& plan);
+
+// Autotuner support.  First-round candidates for n >= 15: the default plan,
+// then every split of bits 10..n-1 into the fewest groups of 5..10 bits (the
+// fewest HBM round trips) with every choice of phase group; run lengths 128 B
+// for plain groups and 64 B for the phase group.
+void plan_candidates(int n, std::vector<PassPlan>& out);
+// Contiguous groups of the given widths from bit 10 up.
+void plan_with_groups(int n, const std::vector<int>& sizes, int phase_group, bool tma, PassPlan& plan);
+void set_tuned_plan(const PassPlan& plan);  // record for (current device, plan.n)
+bool tuned_plan(int n, PassPlan& out);
+void clear_tuned_plans();
 
 // Passes for steps c0 <= k < c1 of the range [k0, k1): P rows are relative to
 // the chunk (row k + 1 - c0 ends step k), B rows likewise (row k - c0).
@@ -48,6 +62,31 @@ cudaError_t launch_planned_pass(const LaunchCtx& lc, const PassPlan& plan, const
                                 const ClauseLP* cl, const float2* ptab, const float2* btab, int* err);
 
 constexpr long long kChunkSteps = 1024;
+
+// Device-driven evolution of a step range in one CUDA graph (graph.cpp): a
+// WHILE conditional node whose body is kGraphUnroll Strang steps, with the
+// phase rows of each iteration computed on the device.
+constexpr int kGraphUnroll = 8;
+struct GraphSpec {
+  const PassPlan* plan = nullptr;
+  float2* psi = nullptr;
+  int m = 0;
+  const ClauseLP* cl = nullptr;
+  int* err = nullptr;  // bounded-wait error word of the TMA passes
+  double dt = 0;
+  const double* s_dev = nullptr;  // caller schedule on the device, or null for s_k = (k + 1/2)/K
+  long long K = 0, k0 = 0, k1 = 0;
+  int num_sms = 0;
+  // graph scratch (graph_scratch_bytes): loop counter, kGraphUnroll + 1 P rows, kGraphUnroll B rows
+  long long* ctr = nullptr;
+  float2* prow = nullptr;
+  float2* brow = nullptr;
+};
+size_t graph_scratch_bytes(int n, int m);
+void graph_scratch_split(void* base, int m, GraphSpec& s);
+// Build and instantiate the graph for s (streaming plans only).  The graph
+// reads and writes s.psi and the scratch; launch it on any stream.
+cudaError_t build_evolve_graph(const GraphSpec& s, cudaGraphExec_t* out);
 
 // Bytes of phase tables for a chunk of `chunk` steps.
 inline size_t table_entries(int n, int m, long long chunk) {

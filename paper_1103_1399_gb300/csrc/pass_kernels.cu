@@ -219,12 +219,39 @@ __global__ void init_uniform_kernel(float2* __restrict__ psi, unsigned long long
     psi[x] = z;
 }
 
-// Phase tables for the steps c0 <= k < c1 of a range [k0, k1) of a K-step run.
-// P row rho (position p = c0 - k0 + rho, the boundary before step k0 + p):
+// Phase-table entries.  P row at boundary position p of a range [k0, k1) of a
+// K-step run (p = 0 before step k0, p = k1 - k0 after the last step):
 //   theta_p = dt/2 ( s_(k0+p-1) [p >= 1] + s_(k0+p) [p < k1-k0] ),  entry E: exp(-i theta_p E)
-// B row rho (step k = c0 + rho):  entry q: 2^-n exp(-i dt (1 - s_k) q)
+// B row of step k:  entry q: 2^-n exp(-i dt (1 - s_k) q)
 // s_k = (k + 1/2)/K, or s_dev[k] for a caller-supplied schedule.  FP64 angles,
-// FP64 sine/cosine, one rounding to FP32 per entry.
+// FP64 sine/cosine, one rounding to FP32 per entry.  Every producer of phase
+// rows (the chunk tables below, the per-iteration rows of a launch graph)
+// calls these two functions, so the rows are identical whichever produced them.
+__device__ __forceinline__ double sched_s(const double* s_dev, long long K, long long k) {
+  return s_dev ? s_dev[k] : (static_cast<double>(k) + 0.5) / static_cast<double>(K);
+}
+
+__device__ __noinline__ float2 p_entry(double dt, const double* s_dev, long long K, long long k0, long long k1,
+                                       long long p, int e) {
+  double th = 0.0;
+  if (p >= 1) th += sched_s(s_dev, K, k0 + p - 1);
+  if (p < k1 - k0) th += sched_s(s_dev, K, k0 + p);
+  th *= 0.5 * dt;
+  double sn, cs;
+  sincos(th * static_cast<double>(e), &sn, &cs);
+  return make_float2(static_cast<float>(cs), static_cast<float>(-sn));
+}
+
+__device__ __noinline__ float2 b_entry(double dt, const double* s_dev, long long K, long long k, int q, double scale) {
+  const double s = sched_s(s_dev, K, k);
+  const double ph = dt * (1.0 - s) * static_cast<double>(q);
+  double sn, cs;
+  sincos(ph, &sn, &cs);
+  return make_float2(static_cast<float>(scale * cs), static_cast<float>(-scale * sn));
+}
+
+// Phase tables for the steps c0 <= k < c1 of a range [k0, k1): P row rho is
+// position p = c0 - k0 + rho, B row rho is step k = c0 + rho.
 __global__ void tables_kernel(float2* __restrict__ ptab, float2* __restrict__ btab, int n, int m, double dt,
                               const double* __restrict__ s_dev, long long K, long long k0, long long k1,
                               long long c0, long long c1, double scale) {
@@ -235,31 +262,50 @@ __global__ void tables_kernel(float2* __restrict__ ptab, float2* __restrict__ bt
     if (i < np) {
       const long long rho = i / (m + 1);
       const int e = static_cast<int>(i - rho * (m + 1));
-      const long long p = c0 - k0 + rho;
-      double th = 0.0;
-      if (p >= 1) {
-        const long long k = k0 + p - 1;
-        th += s_dev ? s_dev[k] : (static_cast<double>(k) + 0.5) / static_cast<double>(K);
-      }
-      if (p < k1 - k0) {
-        const long long k = k0 + p;
-        th += s_dev ? s_dev[k] : (static_cast<double>(k) + 0.5) / static_cast<double>(K);
-      }
-      th *= 0.5 * dt;
-      double sn, cs;
-      sincos(th * static_cast<double>(e), &sn, &cs);
-      ptab[i] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));
+      ptab[i] = p_entry(dt, s_dev, K, k0, k1, c0 - k0 + rho, e);
     } else {
       const long long j = i - np;
       const long long rho = j / (n + 1);
       const int q = static_cast<int>(j - rho * (n + 1));
-      const long long k = c0 + rho;
-      const double s = s_dev ? s_dev[k] : (static_cast<double>(k) + 0.5) / static_cast<double>(K);
-      const double ph = dt * (1.0 - s) * static_cast<double>(q);
-      double sn, cs;
-      sincos(ph, &sn, &cs);
-      btab[j] = make_float2(static_cast<float>(scale * cs), static_cast<float>(-scale * sn));
+      btab[j] = b_entry(dt, s_dev, K, c0 + rho, q, scale);
     }
+  }
+}
+
+// Rows for a launch graph: P positions p_first + j into rows dst_p0 + j of
+// prow (j < nprow), B rows of steps k_first + j into rows j of brow (j <
+// nbrow); with ctr non-null both starts are offset by *ctr (the graph's loop
+// counter, read by every thread; nothing here writes it).
+__global__ void graph_rows_kernel(float2* __restrict__ prow, int dst_p0, long long p_first, int nprow,
+                                  float2* __restrict__ brow, long long k_first, int nbrow,
+                                  const long long* __restrict__ ctr, int n, int m, double dt,
+                                  const double* __restrict__ s_dev, long long K, long long k0, long long k1,
+                                  double scale) {
+  const long long off = ctr ? *ctr : 0;
+  const long long np = static_cast<long long>(nprow) * (m + 1), nb = static_cast<long long>(nbrow) * (n + 1);
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np + nb;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    if (i < np) {
+      const long long j = i / (m + 1);
+      const int e = static_cast<int>(i - j * (m + 1));
+      prow[(dst_p0 + j) * (m + 1) + e] = p_entry(dt, s_dev, K, k0, k1, p_first + off + j, e);
+    } else {
+      const long long t = i - np;
+      const long long j = t / (n + 1);
+      const int q = static_cast<int>(t - j * (n + 1));
+      brow[t] = b_entry(dt, s_dev, K, k_first + off + j, q, scale);
+    }
+  }
+}
+
+// The last node of a graph loop body: advance the counter by `step` and keep
+// looping while it is below `limit`.  The counter only grows, so the loop ends
+// after at most limit / step iterations.
+__global__ void graph_advance_kernel(long long* ctr, long long step, long long limit, cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const long long c = *ctr + step;
+    *ctr = c;
+    cudaGraphSetConditional(h, (c >= 0 && c < limit) ? 1u : 0u);
   }
 }
 
@@ -332,6 +378,25 @@ cudaError_t launch_init_uniform(const LaunchCtx& lc, float2* psi, int n) {
   const long long cap = 8ll * lc.num_sms;
   if (grid > cap) grid = cap;
   init_uniform_kernel<<<static_cast<unsigned>(grid), 256, 0, lc.stream>>>(psi, count, val);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_graph_rows(const LaunchCtx& lc, float2* prow, int dst_p0, long long p_first, int nprow, float2* brow,
+                              long long k_first, int nbrow, const long long* ctr, int n, int m, double dt,
+                              const double* s_dev, long long K, long long k0, long long k1) {
+  const long long total = static_cast<long long>(nprow) * (m + 1) + static_cast<long long>(nbrow) * (n + 1);
+  long long grid = (total + 127) / 128;
+  if (grid > 2ll * lc.num_sms) grid = 2ll * lc.num_sms;
+  if (grid < 1) grid = 1;
+  graph_rows_kernel<<<static_cast<unsigned>(grid), 128, 0, lc.stream>>>(
+      prow, dst_p0, p_first, nprow, brow, k_first, nbrow, ctr, n, m, dt, s_dev, K, k0, k1,
+      exp2(-static_cast<double>(n)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_graph_advance(const LaunchCtx& lc, long long* ctr, long long step, long long limit,
+                                 cudaGraphConditionalHandle h) {
+  graph_advance_kernel<<<1, 32, 0, lc.stream>>>(ctr, step, limit, h);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@
 // the half phases of two steps), the other groups up: 2g-2 HBM round trips for
 // g groups.  n <= 14 runs entirely on chip.
 #include <cstdlib>
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -67,7 +68,103 @@ int encode_clauses(int n, const int32_t* lits, int m, std::vector<ClauseMV>& mv,
   return QAA_OK;
 }
 
+namespace {
+std::mutex g_tuned_mu;
+std::map<std::pair<int, int>, PassPlan> g_tuned;  // (device, n) -> plan chosen by qaa_autotune
+
+bool env_overrides() {
+  for (const char* v : {"QAA_PASSES", "QAA_GROUP_BITS", "QAA_SPLIT_GROUPS", "QAA_PHASE_GROUP", "QAA_RUN128_GROUPS"})
+    if (std::getenv(v)) return true;
+  return false;
+}
+
+int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return d;
+}
+}  // namespace
+
+void set_tuned_plan(const PassPlan& plan) {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  g_tuned[{current_device(), plan.n}] = plan;
+}
+
+void clear_tuned_plans() {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  g_tuned.clear();
+}
+
+bool tuned_plan(int n, PassPlan& out) {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  auto it = g_tuned.find({current_device(), n});
+  if (it == g_tuned.end()) return false;
+  out = it->second;
+  return true;
+}
+
+// Every split of `rest` bits into g ordered groups of 5..10 bits.
+static void compositions(int rest, int g, std::vector<int>& cur, std::vector<std::vector<int>>& out) {
+  if (g == 0) {
+    if (rest == 0) out.push_back(cur);
+    return;
+  }
+  for (int q = 5; q <= 10 && q <= rest; ++q) {
+    cur.push_back(q);
+    compositions(rest - q, g - 1, cur, out);
+    cur.pop_back();
+  }
+}
+
+void plan_with_groups(int n, const std::vector<int>& sizes, int phase_group, bool tma, PassPlan& plan) {
+  plan = PassPlan();
+  plan.n = n;
+  plan.onchip = false;
+  plan.use_tma = tma;
+  int a = kLowBits;
+  for (int q : sizes) {
+    plan.strided.push_back({a, q, a + 5});
+    a += q;
+  }
+  plan.phase_group = phase_group;
+  const int ng = static_cast<int>(sizes.size());
+  plan.run_c.assign(static_cast<size_t>(ng), 0);
+  for (int i = 0; i < ng; ++i) plan.run_c[i] = i == phase_group ? 0 : 4;
+}
+
+void plan_candidates(int n, std::vector<PassPlan>& out) {
+  out.clear();
+  if (n <= kOnchipMaxBits) return;
+  const int rest = n - kLowBits;
+  const int g = (rest + 9) / 10;
+  std::vector<std::vector<int>> comps;
+  std::vector<int> cur;
+  compositions(rest, g, cur, comps);
+  const bool tma = tma_available();
+  PassPlan def;
+  make_default_plan(n, def);
+  out.push_back(def);
+  for (const auto& c : comps)
+    for (int pg = 0; pg < g; ++pg) {
+      PassPlan p;
+      plan_with_groups(n, c, pg, tma, p);
+      bool same = p.strided.size() == def.strided.size() && p.phase_group == def.phase_group;
+      for (size_t i = 0; same && i < p.strided.size(); ++i)
+        same = p.strided[i].a == def.strided[i].a && p.strided[i].q == def.strided[i].q &&
+               p.strided[i].a2 == def.strided[i].a2;
+      if (!same) out.push_back(p);
+    }
+}
+
 void make_plan(int n, PassPlan& plan) {
+  if (n > kOnchipMaxBits && !env_overrides() && tuned_plan(n, plan)) return;
+  make_default_plan(n, plan);
+}
+
+void make_default_plan(int n, PassPlan& plan) {
   plan = PassPlan();
   plan.n = n;
   plan.onchip = n <= kOnchipMaxBits;

@@ -74,6 +74,15 @@ cudaError_t launch_tables(const LaunchCtx& lc, float2* ptab, float2* btab, int n
                           const double* s_dev, long long K, long long k0, long long k1, long long c0, long long c1);
 cudaError_t launch_pass(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m,
                         const ClauseLP* cl, const float2* ptab, const float2* btab);
+// Launch-graph helpers: phase rows from the same entry functions as
+// launch_tables (P positions p_first + j -> rows dst_p0 + j, B steps k_first + j
+// -> rows j, both offset by *ctr when ctr is non-null), and the loop-body tail
+// that advances *ctr by `step` and sets the WHILE condition to *ctr < limit.
+cudaError_t launch_graph_rows(const LaunchCtx& lc, float2* prow, int dst_p0, long long p_first, int nprow, float2* brow,
+                              long long k_first, int nbrow, const long long* ctr, int n, int m, double dt,
+                              const double* s_dev, long long K, long long k0, long long k1);
+cudaError_t launch_graph_advance(const LaunchCtx& lc, long long* ctr, long long step, long long limit,
+                                 cudaGraphConditionalHandle h);
 // n <= kOnchipMaxBits: the whole state stays in one CTA's shared memory for
 // `nsteps` steps.  P row j (j = 0..nsteps) and B row j (j < nsteps) as produced
 // by launch_tables; first_p = apply P row 0 before the first transform.

@@ -130,21 +130,29 @@ struct Req {
   long long chunk = 0;
   unsigned* d_bar = nullptr;
   cudaEvent_t done_ev = nullptr;
+  cudaGraphExec_t gexec = nullptr;  // launch graph of a streamed request, kept until it completes
   bool persist = false;  // mid-size: one persistent cooperative launch for the whole run
+  bool graph = false;    // streamed: one launch graph for the whole run
   bool small() const { return plan.onchip; }
   bool persistent() const { return persist; }
 };
 
-// Device bytes of one request: state, clause tables, phase tables (the whole
-// run for on-chip requests, a chunk of at most 1024 steps otherwise),
-// reduction partials, results and an error word.
-size_t request_bytes(int n, int m, long long K, long long chunk, int num_sms) {
+// Phase-table bytes of a request: the whole run for on-chip and persistent
+// requests, the graph scratch (8 steps of rows) for launch-graph requests, a
+// chunk of at most 1024 steps for per-pass launches.
+size_t table_bytes(int n, int m, long long K, bool whole_run, bool graph) {
+  if (graph) return qaa::graph_scratch_bytes(n, m);
+  return 8u * qaa::table_entries(n, m, whole_run ? K : std::min(qaa::kChunkSteps, K));
+}
+
+// Device bytes of one request: state, clause tables, phase tables, reduction
+// partials, results, an error word and a grid-barrier word pair.
+size_t request_bytes(int n, int m, size_t tab_bytes, int num_sms) {
   size_t b = align_up((static_cast<size_t>(8) << n));
   b += align_up(16u * static_cast<size_t>(std::max(m, 1))) * 2;
-  b += align_up(8u * qaa::table_entries(n, m, chunk));
+  b += align_up(tab_bytes);
   b += align_up(8u * qaa::obs_partials_len(n, num_sms));
   b += align_up(64) + align_up(16) + align_up(16);
-  (void)K;
   return b;
 }
 
@@ -185,6 +193,7 @@ struct qaa_server {
   int persist_turn = 0;
   int persist_grid = 32;      // CTAs per persistent request, at most
   int persist_max_bits = 0;   // largest n served by a persistent launch (0: none)
+  bool use_graphs = true;     // streamed requests: one launch graph each
   // small-request batches
   cudaStream_t batch_stream = nullptr;
   qaa::OnchipJob* h_jobs[2] = {nullptr, nullptr};
@@ -212,6 +221,10 @@ void release(qaa_server* s, Req* r) {
     cudaEventDestroy(r->done_ev);
     r->done_ev = nullptr;
   }
+  if (r->gexec) {
+    cudaGraphExecDestroy(r->gexec);
+    r->gexec = nullptr;
+  }
   if (r->bytes) {
     s->arena.release(r->off, r->bytes);
     r->bytes = 0;
@@ -225,7 +238,8 @@ void release(qaa_server* s, Req* r) {
 // Carve the request's device block and upload its clause tables (on `stream`).
 bool place(qaa_server* s, Req* r) {
   r->chunk = (r->small() || r->persistent()) ? r->K : std::min(qaa::kChunkSteps, r->K);
-  const size_t need = request_bytes(r->n, r->m, r->K, r->chunk, s->num_sms);
+  const size_t tb = table_bytes(r->n, r->m, r->K, r->small() || r->persistent(), r->graph);
+  const size_t need = request_bytes(r->n, r->m, tb, s->num_sms);
   if (s->free_slots.empty()) return false;
   size_t off = 0;
   if (!s->arena.alloc(need, &off)) return false;
@@ -242,7 +256,7 @@ bool place(qaa_server* s, Req* r) {
   r->psi = reinterpret_cast<float2*>(take(static_cast<size_t>(8) << r->n));
   r->d_mv = reinterpret_cast<qaa::ClauseMV*>(take(16u * std::max(r->m, 1)));
   r->d_lp = reinterpret_cast<qaa::ClauseLP*>(take(16u * std::max(r->m, 1)));
-  r->d_tab = reinterpret_cast<float2*>(take(8u * qaa::table_entries(r->n, r->m, r->chunk)));
+  r->d_tab = reinterpret_cast<float2*>(take(tb));
   r->d_part = reinterpret_cast<double*>(take(8u * qaa::obs_partials_len(r->n, s->num_sms)));
   r->d_res = reinterpret_cast<double*>(take(64));
   r->d_err = reinterpret_cast<int*>(take(16));
@@ -277,12 +291,31 @@ cudaError_t observe_async(qaa_server* s, Req* r, cudaStream_t st) {
   return e;
 }
 
-// The streaming evolution of one request (issuer thread, its own stream).
+// The streaming evolution of one request (issuer thread, its own stream):
+// one launch graph for the whole run, or one launch per pass.
 cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
   cudaError_t e = upload_tables(s, r, st);
   if (e == cudaSuccess) e = qaa::launch_init_uniform(lc, r->psi, r->n);
   const double dt = r->T / static_cast<double>(r->K);
+  if (r->graph) {
+    qaa::GraphSpec gs;
+    gs.plan = &r->plan;
+    gs.psi = r->psi;
+    gs.m = r->m;
+    gs.cl = r->d_lp;
+    gs.err = r->d_err;
+    gs.dt = dt;
+    gs.K = r->K;
+    gs.k0 = 0;
+    gs.k1 = r->K;
+    gs.num_sms = s->num_sms;
+    qaa::graph_scratch_split(r->d_tab, r->m, gs);
+    if (e == cudaSuccess) e = qaa::build_evolve_graph(gs, &r->gexec);
+    if (e == cudaSuccess) e = cudaGraphLaunch(r->gexec, st);
+    if (e == cudaSuccess) e = observe_async(s, r, st);
+    return e;
+  }
   float2* ptab = r->d_tab;
   float2* btab = r->d_tab + static_cast<size_t>(r->chunk + 1) * (r->m + 1);
   std::vector<qaa::Pass> passes;
@@ -340,6 +373,7 @@ void issuer_main(qaa_server* s, int idx) {
     }
     const cudaError_t e = issue_streaming(s, r, st);
     if (e != cudaSuccess) {
+      cudaStreamSynchronize(st);  // work already queued must finish before the block is reused
       cudaGetLastError();
       r->status = QAA_E_CUDA;  // reported when the worker picks it up
     }
@@ -457,6 +491,7 @@ void worker_main(qaa_server* s) {
         cudaStream_t st = s->persist_streams[s->persist_turn];
         s->persist_turn = (s->persist_turn + 1) % static_cast<int>(s->persist_streams.size());
         if (issue_persistent(s, r, st) != cudaSuccess) {
+          cudaStreamSynchronize(st);
           cudaGetLastError();
           r->status = QAA_E_CUDA;
         }
@@ -563,6 +598,7 @@ int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) 
   s->persist_max_bits = 17;
   if (const char* v = std::getenv("QAA_PERSIST_MAX_BITS")) s->persist_max_bits = std::min(std::atoi(v), qaa::kPersistMaxBits);
   if (const char* v = std::getenv("QAA_PERSIST_GRID")) s->persist_grid = std::max(1, std::atoi(v));
+  if (const char* v = std::getenv("QAA_SERVER_GRAPHS")) s->use_graphs = std::atoi(v) != 0;
   if (cudaMallocHost(&s->h_res, sizeof(double) * 8 * max_slots) != cudaSuccess ||
       cudaMallocHost(&s->h_stage, kStageBytes * static_cast<size_t>(max_slots)) != cudaSuccess)
     return bail(QAA_E_NOMEM, "cannot allocate result slots");
@@ -623,13 +659,13 @@ int qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, in
   // Persistent launches keep the phase tables of the whole run resident, so
   // they take runs of at most kPersistMaxSteps steps.
   r->persist = !r->plan.onchip && n <= s->persist_max_bits && steps <= kPersistMaxSteps;
-  const long long chunk = (r->plan.onchip || r->persist) ? static_cast<long long>(steps)
-                                                         : std::min<long long>(qaa::kChunkSteps, steps);
+  r->graph = !r->plan.onchip && !r->persist && s->use_graphs;
   if (r->plan.onchip && qaa::onchip_smem_bytes(n, m) > 227u * 1024u) {
     delete r;
     return sfail(QAA_E_ARG, "instance too large for the on-chip evolver");
   }
-  const size_t need = request_bytes(n, m, steps, chunk, s->num_sms);
+  const size_t need =
+      request_bytes(n, m, table_bytes(n, m, steps, r->plan.onchip || r->persist, r->graph), s->num_sms);
   if (need > s->arena.size()) {
     delete r;
     return sfail(QAA_E_NOMEM, "request needs " + std::to_string(need) + " device bytes, more than the server's " +
@@ -742,6 +778,7 @@ int qaa_server_destroy(qaa_server* s) {
   cudaFreeHost(s->h_stage);
   for (auto& kv : s->all) {
     if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
+    if (kv.second->gexec) cudaGraphExecDestroy(kv.second->gexec);
     delete kv.second;
   }
   delete s;

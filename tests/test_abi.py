@@ -76,3 +76,48 @@ def test_flatten_pads_short_clauses(q):
     assert list(buf) == [1, 0, 0, 2, -3, 0, 4, 5, -6]
     with pytest.raises(ValueError):
         q.flatten_clauses([[1, 2, 3, 4]])
+
+
+def _compositions(rest, g):
+    if g == 0:
+        return 1 if rest == 0 else 0
+    return sum(_compositions(rest - q, g - 1) for q in range(5, 11) if q <= rest)
+
+
+def _group_bits(desc):
+    """Bit positions of every strided group in a plan description, and how many host the phase."""
+    bits, phase = [], 0
+    for part in desc.split("; "):
+        if not part.startswith("group bits "):
+            continue
+        for a, b in re.findall(r"\[(\d+),(\d+)\)", part):
+            bits.extend(range(int(a), int(b)))
+        phase += part.endswith("W.B.W") or " W.B.W " in part
+    return sorted(bits), phase
+
+
+@pytest.mark.parametrize("n", [10, 14, 15, 17, 20, 21, 24, 25, 28, 30, 32, 34])
+def test_autotune_candidates_cover_every_split(q, n):
+    descs = q.tune_candidates(n)
+    if n <= 14:
+        assert descs == []
+        return
+    rest = n - 10
+    g = (rest + 9) // 10
+    full = _compositions(rest, g) * g
+    # the default plan comes first; when it is one of the contiguous splits it is not repeated
+    assert len(descs) in (full, full + 1)
+    assert len(set(descs)) == len(descs)
+    widths = set()
+    for d in descs:
+        bits, phase = _group_bits(d)
+        assert bits == list(range(10, n)), d  # every bit above the low pass exactly once
+        assert phase == 1, d
+        widths.add(tuple(int(b) - int(a) for a, b in re.findall(r"group bits \[(\d+),(\d+)\)", d)))
+    # every first-half width 5 appears: e.g. n = 25 offers 5+10, 6+9, ..., 10+5
+    assert len(descs) >= _compositions(rest, g)
+
+
+def test_autotune_candidates_argument_check(q):
+    with pytest.raises(q.QaaError):
+        q.tune_candidates(0)
