@@ -222,8 +222,30 @@ def _pct(v, p):
     return float(np.percentile(np.asarray(v), p)) if v else None
 
 
+def autotune_sizes(q, torch, work):
+    """qaa_autotune once per streaming size of the mix (n >= 15), on the first
+    request of that size; the chosen plans then serve every later handle and
+    server request of that n in this process."""
+    out, t0 = {}, time.perf_counter()
+    seen = {}
+    for n, cl, _, _ in work:
+        if n >= 15 and n not in seen:
+            seen[n] = cl
+    for n in sorted(seen):
+        psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+        with q.Instance(n, seen[n]) as inst:
+            # enough steps that one timing lasts about a millisecond or more
+            rep = inst.autotune(psi, steps=max(3, min(64, 1 << max(0, 26 - n))), budget_ms=5000)
+            out[str(n)] = {"chosen": inst.describe_plan(),
+                           "candidates": sum(1 for ln in rep.splitlines() if "ms/step" in ln and not ln.startswith("chosen"))}
+        del psi
+    torch.cuda.synchronize()
+    return {"seconds": time.perf_counter() - t0, "plans": out}
+
+
 def run_serving(q, torch, work, rate_factor=0.7):
     out = {"requests": len(work), "dt": SERVE_DT, "mix": "n ~ U{10..22}, T ~ U[5,80], planted unique-solution"}
+    out["autotune"] = autotune_sizes(q, torch, work)
     # baseline: one launch sequence per instance, one after another (handle API)
     t0 = time.perf_counter()
     lat = []
@@ -374,6 +396,52 @@ def run_ours(args):
                               "hbm_gbs": passes_per_step * 2 * state_bytes * vk / (vms / 1e3) / 1e9}
             vi.close()
 
+    # launch-graph mode on the same workload: one CUDA graph per evolve call
+    graph = None
+    if not args.no_variants:
+        gi = q.Instance(n, clauses, stream=stream)
+        gi.set_launch_mode(q.LAUNCH_GRAPH)
+        gk = min(K, 100)
+        gi.init_uniform(psi)
+        gi.evolve(psi, DT * gk, gk)  # builds the graph (and warms up)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        gi.evolve(psi, DT * gk, gk)  # same arguments: the graph is relaunched
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1)
+        graph = {"steps_per_s": gk / (gms / 1e3), "ms_per_step": gms / gk, "steps": gk,
+                 "what": "qaa_set_launch_mode(QAA_LAUNCH_GRAPH): one graph launch per evolve call, a device-side "
+                         "WHILE loop over 8-step bodies"}
+        gi.close()
+
+    # the 32-qubit case of the same configuration (32 GiB state), a short run
+    n32 = None
+    if not args.no_n32 and rank == 0:
+        psi = None  # room for the 32 GiB state
+        torch.cuda.empty_cache()
+        d32 = satgen.load_instance("planted_n32_s0")
+        p32 = torch.empty(1 << 32, dtype=torch.complex64, device="cuda")
+        i32 = q.Instance(32, d32["clauses"], stream=stream)
+        k32 = 12
+        i32.init_uniform(p32)
+        i32.evolve(p32, DT * 3, 3)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        i32.evolve(p32, DT * k32, k32)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        hms = h0.elapsed_time(h1)
+        rts = 2 * (i32.describe_plan().count("group bits"))
+        n32 = {"steps_per_s": k32 / (hms / 1e3), "ms_per_step": hms / k32, "steps": k32, "plan": i32.describe_plan(),
+               "hbm_gbs": rts * 2 * 8 * (1 << 32) * k32 / (hms / 1e3) / 1e9, "m": len(d32["clauses"])}
+        i32.close()
+        del p32
+        torch.cuda.empty_cache()
+        psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+
     # e2e: a full solve through the public API with the instance in host memory
     e2e = None
     if not args.no_e2e:
@@ -424,6 +492,8 @@ def run_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
             "precision_variants": variants,
+            "launch_graph": graph,
+            "n32": n32,
             "serving": serving,
             "cpu_baseline": cpu,
             "final": {"norm": obs["norm"], "ground_prob": obs["ground_prob"]},
@@ -443,7 +513,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-variants", action="store_true", help="skip timing the tensor-core WHT variants")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip timing the tensor-core WHT variants and the launch-graph mode")
+    ap.add_argument("--no-n32", action="store_true", help="skip the short 32-qubit (32 GiB) run")
     ap.add_argument("--serving-requests", type=int, default=1024,
                     help="requests in the batched-serving measurement (0 skips it)")
     ap.add_argument("--instance", default=INSTANCE,

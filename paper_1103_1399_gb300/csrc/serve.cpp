@@ -193,7 +193,12 @@ struct qaa_server {
   int persist_turn = 0;
   int persist_grid = 32;      // CTAs per persistent request, at most
   int persist_max_bits = 0;   // largest n served by a persistent launch (0: none)
-  bool use_graphs = true;     // streamed requests: one launch graph each
+  // Streamed requests as one launch graph each (QAA_SERVER_GRAPHS=1).  Off by
+  // default: on the n ~ U{10..22} mix it measured 202-210 solves/s (4 or 8
+  // issuers) against 219 with per-pass launches from 4 issuers -- the graph
+  // makes one request's steps faster but several n = 20..22 requests then
+  // contend for L2 and HBM at once.
+  bool use_graphs = false;
   // small-request batches
   cudaStream_t batch_stream = nullptr;
   qaa::OnchipJob* h_jobs[2] = {nullptr, nullptr};
@@ -616,7 +621,8 @@ int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) 
   cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
   if (cudaStreamCreateWithPriority(&s->batch_stream, cudaStreamNonBlocking, hi_pri) != cudaSuccess)
     return bail(QAA_E_CUDA, "cannot create streams");
-  const int nissuers = 4;
+  int nissuers = 4;  // QAA_SERVER_ISSUERS overrides (1..32)
+  if (const char* v = std::getenv("QAA_SERVER_ISSUERS")) nissuers = std::min(32, std::max(1, std::atoi(v)));
   for (int i = 0; i < nissuers; ++i) {
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo_pri) != cudaSuccess)
