@@ -379,21 +379,27 @@ def run_ours(args):
     # tensor-core split-BF16 Walsh-Hadamard variants on the same workload
     variants = {}
     if not args.no_variants:
-        for kind, name in ((1, "bf16x3"), (2, "bf16x2")):
+        for kind, name in ((1, "bf16x3"), (2, "bf16x2"), (3, "rotation")):
             vi = q.Instance(n, clauses, stream=stream)
             vi.set_variant(kind)
             vi.init_uniform(psi)
             vk = min(K, 100)
             vi.evolve(psi, DT * 3, 3)
             torch.cuda.synchronize()
+            vi.profile(True)
+            vi.profile_reset()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             vi.evolve(psi, DT * vk, vk)
             e1.record(stream)
             torch.cuda.synchronize()
             vms = e0.elapsed_time(e1)
+            vprof = {k: {"launches": v[0], "ms": v[1]} for k, v in vi.profile_read().items() if v[0] > 0}
+            vi.profile(False)
+            rts = passes_per_step if kind != 3 else vi.describe_plan().count("group bits") + 1
             variants[name] = {"steps_per_s": vk / (vms / 1e3), "ms_per_step": vms / vk, "steps": vk,
-                              "hbm_gbs": passes_per_step * 2 * state_bytes * vk / (vms / 1e3) / 1e9}
+                              "hbm_round_trips_per_step": rts, "plan": vi.describe_plan(), "kernels": vprof,
+                              "hbm_gbs": rts * 2 * state_bytes * vk / (vms / 1e3) / 1e9}
             vi.close()
 
     # launch-graph mode on the same workload: one CUDA graph per evolve call
@@ -437,6 +443,19 @@ def run_ours(args):
         rts = 2 * (i32.describe_plan().count("group bits"))
         n32 = {"steps_per_s": k32 / (hms / 1e3), "ms_per_step": hms / k32, "steps": k32, "plan": i32.describe_plan(),
                "hbm_gbs": rts * 2 * 8 * (1 << 32) * k32 / (hms / 1e3) / 1e9, "m": len(d32["clauses"])}
+        if not args.no_variants:
+            i32.set_variant(3)
+            i32.init_uniform(p32)
+            i32.evolve(p32, DT * 3, 3)
+            torch.cuda.synchronize()
+            h0.record(stream)
+            i32.evolve(p32, DT * k32, k32)
+            h1.record(stream)
+            torch.cuda.synchronize()
+            rms = h0.elapsed_time(h1)
+            rrt = i32.describe_plan().count("group bits") + 1
+            n32["rotation"] = {"steps_per_s": k32 / (rms / 1e3), "ms_per_step": rms / k32, "plan": i32.describe_plan(),
+                               "hbm_gbs": rrt * 2 * 8 * (1 << 32) * k32 / (rms / 1e3) / 1e9}
         i32.close()
         del p32
         torch.cuda.empty_cache()

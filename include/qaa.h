@@ -95,6 +95,14 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream);
  *               amplitude split into three BF16 parts (hi + mid + lo), FP32
  *               accumulation: about FP32 accuracy.
  *            2: as 1 with two parts (hi + lo): about 16 mantissa bits.
+ *            3: rotation form: exp(-i theta H_B) applied directly as the product
+ *               of its n one-qubit factors (H_B = sum_i (1 - sigma^x_i)/2 is a
+ *               sum of commuting one-qubit terms, Sec. 2.1), each
+ *               (|+><+| + e^(-i theta) |-><-|), as complex butterflies inside
+ *               the same passes; no Walsh-Hadamard change of basis, so g HBM
+ *               round trips per step instead of 2g - 2 (3 instead of 4 at
+ *               n = 30).  Same Strang step, FP32 butterflies; needs the TMA
+ *               passes (QAA_E_ARG otherwise).
  *   q        reserved for the qubits-per-pass choice; only 0 (automatic).
  * Returns QAA_E_ARG for an unknown kind or q != 0.
  */

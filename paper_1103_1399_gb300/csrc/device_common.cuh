@@ -43,6 +43,21 @@ __device__ __forceinline__ void reg_wht(float2 (&v)[32]) {
   }
 }
 
+// exp(-i theta H_B) on the register-index bits [0, B) of a 32-entry register
+// tile, up to a factor 2^B.  H_B = sum_i (1 - sigma^x_i)/2 (Sec. 2.1) is a sum of
+// commuting one-qubit terms, so on any block of qubits its exponential is
+// W diag(exp(-i theta popcount)) W over that block alone: B butterfly levels,
+// one multiply by tab[popcount(r)] (tab[p] = exp(-i theta p), p = 0..5, FP64
+// rounded once), B levels again.  The factor 2^B is removed by one exact
+// power-of-two scale per step.
+template <int B>
+__device__ __forceinline__ void reg_rot(float2 (&v)[32], const float2 (&tab)[6]) {
+  reg_wht<0, B>(v);
+#pragma unroll
+  for (int r = 0; r < 32; ++r) v[r] = cmul(v[r], tab[__builtin_popcount(r & ((1 << B) - 1))]);
+  reg_wht<0, B>(v);
+}
+
 // Runtime-bounded variant (bits [b0, b1) with b0, b1 in [0, 5]).
 __device__ __forceinline__ void reg_wht_rt(float2 (&v)[32], int b0, int b1) {
 #pragma unroll

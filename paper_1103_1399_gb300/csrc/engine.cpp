@@ -167,6 +167,17 @@ int check_device_error(qaa_ctx* h) {
   return QAA_OK;
 }
 
+// Profiler kind of a pass: the rotation form's passes count as the low-pass
+// and strided kinds they replace.
+int prof_kind(int pass_kind) {
+  switch (pass_kind) {
+    case qaa::kLpPhase: return QAA_K_LOW_FIRST;
+    case qaa::kLpRot: return QAA_K_LOW_MERGE;
+    case qaa::kSpRot: return QAA_K_STRIDED;
+    default: return pass_kind;
+  }
+}
+
 // Streaming plan, launch-graph mode: build (or reuse) the graph of the whole
 // range and launch it.  The graph is rebuilt when psi, the schedule, the range,
 // the variant or the stream changes.
@@ -245,7 +256,8 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
   for (long long c0 = k0; c0 < k1; c0 += chunk) {
     const long long c1 = std::min(k1, c0 + chunk);
     QAA_CK(timed(h, QAA_K_TABLES, [&] {
-      return qaa::launch_tables(lc, ptab, btab, h->n, h->m, dt, s_dev, K, k0, k1, c0, c1);
+      return qaa::launch_tables(lc, ptab, btab, h->n, h->m, dt, s_dev, K, k0, k1, c0, c1,
+                                h->n > qaa::kOnchipMaxBits && h->plan.wht_kind == qaa::kRotationForm);
     }));
     if (h->n <= qaa::kOnchipMaxBits) {
       QAA_CK(timed(h, QAA_K_ONCHIP, [&] {
@@ -254,7 +266,7 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
     } else {
       qaa::build_passes(h->plan, k0, k1, c0, c1, passes);
       for (const qaa::Pass& ps : passes)
-        QAA_CK(timed(h, ps.kind, [&] {
+        QAA_CK(timed(h, prof_kind(ps.kind), [&] {
           return qaa::launch_planned_pass(lc, h->plan, ps, p, h->m, h->d_lp, ptab, btab, h->d_err);
         }));
     }
@@ -378,8 +390,14 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream) {
 
 int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (!h) return fail(QAA_E_ARG, "null handle");
-  if (wht_kind < 0 || wht_kind > 2) return fail(QAA_E_ARG, "unknown wht_kind (0 = FP32, 1 = BF16x3, 2 = BF16x2)");
+  if (wht_kind < 0 || wht_kind > 3)
+    return fail(QAA_E_ARG, "unknown wht_kind (0 = FP32, 1 = BF16x3, 2 = BF16x2, 3 = rotation form)");
   if (q != 0) return fail(QAA_E_ARG, "only automatic qubits-per-pass (q = 0) is available");
+  if (wht_kind == qaa::kRotationForm && h->n > qaa::kOnchipMaxBits && !h->plan.use_tma)
+    return fail(QAA_E_ARG, "the rotation form needs the TMA passes (not available, or QAA_PASSES=classic)");
+  // The rotation form keeps the plan's run lengths: measured at n = 30, 128-byte
+  // runs for the split group and 64-byte runs (three CTAs per SM) for the
+  // contiguous one gave 11.36 ms per step, 128-byte runs for both 11.82 ms.
   h->plan.wht_kind = wht_kind;
   return QAA_OK;
 }

@@ -16,6 +16,8 @@ namespace qaa {
 int encode_clauses(int n, const int32_t* lits, int m, std::vector<ClauseMV>& mv, std::vector<ClauseLP>& lp,
                    std::string& err);
 
+constexpr int kRotationForm = 3;  // PassPlan::wht_kind of the rotation form
+
 struct Group {
   int a, q, a2;  // active bits [a, a+5) and [a2, a2+q-5); a2 == a + 5 for a contiguous group
 };
@@ -25,7 +27,7 @@ struct PassPlan {
   int n = 0;
   bool onchip = false;
   bool use_tma = true;       // TMA-pipelined passes (QAA_PASSES=classic: plain loads)
-  int wht_kind = 0;          // 0 FP32 butterflies, 1/2 tensor-core BF16x3/x2
+  int wht_kind = 0;          // 0 FP32 butterflies, 1/2 tensor-core BF16x3/x2, 3 rotation form
   std::vector<Group> strided;  // ascending bit order
   int phase_group = 0;         // strided group whose pass fuses W B W
   std::vector<int> run_c;      // per strided group: 4 = 128-byte runs, 0 = default

@@ -242,8 +242,16 @@ __device__ __noinline__ float2 p_entry(double dt, const double* s_dev, long long
   return make_float2(static_cast<float>(cs), static_cast<float>(-sn));
 }
 
-__device__ __noinline__ float2 b_entry(double dt, const double* s_dev, long long K, long long k, int q, double scale) {
+// With rot set (rotation form) the row instead holds exp(-i dt (1 - s_k) q)
+// unscaled for q = 0..5, the rest zero: the per-block popcount phases of the
+// rotation form's 5-qubit Walsh-Hadamard sandwiches.
+__device__ __noinline__ float2 b_entry(double dt, const double* s_dev, long long K, long long k, int q, double scale,
+                                       int rot) {
   const double s = sched_s(s_dev, K, k);
+  if (rot) {
+    if (q > 5) return make_float2(0.f, 0.f);
+    scale = 1.0;
+  }
   const double ph = dt * (1.0 - s) * static_cast<double>(q);
   double sn, cs;
   sincos(ph, &sn, &cs);
@@ -254,7 +262,7 @@ __device__ __noinline__ float2 b_entry(double dt, const double* s_dev, long long
 // position p = c0 - k0 + rho, B row rho is step k = c0 + rho.
 __global__ void tables_kernel(float2* __restrict__ ptab, float2* __restrict__ btab, int n, int m, double dt,
                               const double* __restrict__ s_dev, long long K, long long k0, long long k1,
-                              long long c0, long long c1, double scale) {
+                              long long c0, long long c1, double scale, int rot) {
   const long long prow_n = c1 - c0 + 1, brow_n = c1 - c0;
   const long long np = prow_n * (m + 1), nb = brow_n * (n + 1);
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np + nb;
@@ -267,7 +275,7 @@ __global__ void tables_kernel(float2* __restrict__ ptab, float2* __restrict__ bt
       const long long j = i - np;
       const long long rho = j / (n + 1);
       const int q = static_cast<int>(j - rho * (n + 1));
-      btab[j] = b_entry(dt, s_dev, K, c0 + rho, q, scale);
+      btab[j] = b_entry(dt, s_dev, K, c0 + rho, q, scale, rot);
     }
   }
 }
@@ -280,7 +288,7 @@ __global__ void graph_rows_kernel(float2* __restrict__ prow, int dst_p0, long lo
                                   float2* __restrict__ brow, long long k_first, int nbrow,
                                   const long long* __restrict__ ctr, int n, int m, double dt,
                                   const double* __restrict__ s_dev, long long K, long long k0, long long k1,
-                                  double scale) {
+                                  double scale, int rot) {
   const long long off = ctr ? *ctr : 0;
   const long long np = static_cast<long long>(nprow) * (m + 1), nb = static_cast<long long>(nbrow) * (n + 1);
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np + nb;
@@ -293,7 +301,7 @@ __global__ void graph_rows_kernel(float2* __restrict__ prow, int dst_p0, long lo
       const long long t = i - np;
       const long long j = t / (n + 1);
       const int q = static_cast<int>(t - j * (n + 1));
-      brow[t] = b_entry(dt, s_dev, K, k_first + off + j, q, scale);
+      brow[t] = b_entry(dt, s_dev, K, k_first + off + j, q, scale, rot);
     }
   }
 }
@@ -383,14 +391,14 @@ cudaError_t launch_init_uniform(const LaunchCtx& lc, float2* psi, int n) {
 
 cudaError_t launch_graph_rows(const LaunchCtx& lc, float2* prow, int dst_p0, long long p_first, int nprow, float2* brow,
                               long long k_first, int nbrow, const long long* ctr, int n, int m, double dt,
-                              const double* s_dev, long long K, long long k0, long long k1) {
+                              const double* s_dev, long long K, long long k0, long long k1, bool rot) {
   const long long total = static_cast<long long>(nprow) * (m + 1) + static_cast<long long>(nbrow) * (n + 1);
   long long grid = (total + 127) / 128;
   if (grid > 2ll * lc.num_sms) grid = 2ll * lc.num_sms;
   if (grid < 1) grid = 1;
   graph_rows_kernel<<<static_cast<unsigned>(grid), 128, 0, lc.stream>>>(
       prow, dst_p0, p_first, nprow, brow, k_first, nbrow, ctr, n, m, dt, s_dev, K, k0, k1,
-      exp2(-static_cast<double>(n)));
+      exp2(-static_cast<double>(n)), rot ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -401,13 +409,14 @@ cudaError_t launch_graph_advance(const LaunchCtx& lc, long long* ctr, long long 
 }
 
 cudaError_t launch_tables(const LaunchCtx& lc, float2* ptab, float2* btab, int n, int m, double dt,
-                          const double* s_dev, long long K, long long k0, long long k1, long long c0, long long c1) {
+                          const double* s_dev, long long K, long long k0, long long k1, long long c0, long long c1,
+                          bool rot) {
   const long long total = (c1 - c0 + 1) * (m + 1) + (c1 - c0) * (n + 1);
   long long grid = (total + 255) / 256;
   if (grid > 4ll * lc.num_sms) grid = 4ll * lc.num_sms;
   if (grid < 1) grid = 1;
   tables_kernel<<<static_cast<unsigned>(grid), 256, 0, lc.stream>>>(ptab, btab, n, m, dt, s_dev, K, k0, k1, c0, c1,
-                                                                    exp2(-static_cast<double>(n)));
+                                                                    exp2(-static_cast<double>(n)), rot ? 1 : 0);
   return cudaGetLastError();
 }
 

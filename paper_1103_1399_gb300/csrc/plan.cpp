@@ -221,9 +221,31 @@ void make_default_plan(int n, PassPlan& plan) {
     plan.run_c[i] = rmask >= 0 ? (((rmask >> i) & 1) ? 4 : 0) : (i == plan.phase_group ? 0 : 4);
 }
 
+// Rotation form (variant 3): exp(-i theta H_B) = prod_i exp(-i theta (1 - sigma^x_i)/2),
+// one-qubit factors on disjoint qubits, so every group is transformed once per
+// step in any order and no pass changes basis.  A range starts with P alone;
+// step k is the strided groups' rotations, then the low pass's rotations and
+// the P phase at the boundary after step k (merged with the next step's first
+// half, or the last half at the end of the range): g round trips per step.
+static void build_rot_passes(const PassPlan& plan, long long k0, long long c0, long long c1, std::vector<Pass>& out) {
+  if (c0 == k0) out.push_back({kLpPhase, 0, 0, 0, 0, 0, 0});
+  for (long long k = c0; k < c1; ++k) {
+    const int brow = static_cast<int>(k - c0);
+    for (size_t i = 0; i < plan.strided.size(); ++i) {
+      const Group& g = plan.strided[i];
+      out.push_back({kSpRot, g.a, g.q, 0, plan.run_c[i], brow, g.a2});
+    }
+    out.push_back({kLpRot, 0, 0, static_cast<int>(k + 1 - c0), 0, brow, 0});
+  }
+}
+
 void build_passes(const PassPlan& plan, long long k0, long long k1, long long c0, long long c1,
                   std::vector<Pass>& out) {
   out.clear();
+  if (plan.wht_kind == kRotationForm) {
+    build_rot_passes(plan, k0, c0, c1, out);
+    return;
+  }
   const int ng = static_cast<int>(plan.strided.size());
   const int pg = plan.phase_group;
   const Group top = plan.strided[pg];
@@ -258,6 +280,16 @@ void build_passes(const PassPlan& plan, long long k0, long long k1, long long c0
 std::string describe_plan(const PassPlan& plan) {
   if (plan.onchip) return "on-chip: whole run in one CTA's shared memory (n=" + std::to_string(plan.n) + ")";
   const int ng = static_cast<int>(plan.strided.size());
+  if (plan.wht_kind == kRotationForm) {
+    std::string d = "streaming, TMA loads, rotation form (H_B as one-qubit rotations); low pass bits [0,10) R.P";
+    for (int i = 0; i < ng; ++i) {
+      const Group& g = plan.strided[i];
+      d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";
+      if (g.q > 5) d += "+[" + std::to_string(g.a2) + "," + std::to_string(g.a2 + g.q - 5) + ")";
+      d += plan.run_c[i] == 4 ? " R 128B runs" : " R 64B runs";
+    }
+    return d + "; " + std::to_string(ng + 1) + " HBM round trips per step";
+  }
   const char* wk = plan.wht_kind == 1 ? "tensor-core BF16x3" : (plan.wht_kind == 2 ? "tensor-core BF16x2" : "FP32");
   std::string d = "streaming, " + std::string(plan.wht_kind ? "plain" : (plan.use_tma ? "TMA" : "classic")) +
                   " loads, " + wk + " WHT; low pass bits [0,10) W.P.W";
@@ -287,6 +319,7 @@ cudaError_t allow_smem(const void* func, size_t bytes) {
 
 cudaError_t launch_planned_pass(const LaunchCtx& lc, const PassPlan& plan, const Pass& p, float2* psi, int m,
                                 const ClauseLP* cl, const float2* ptab, const float2* btab, int* err) {
+  if (plan.wht_kind == kRotationForm) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err);
   if (plan.wht_kind) return launch_pass_tc(lc, p, psi, plan.n, m, cl, ptab, btab, plan.wht_kind == 1 ? 3 : 2);
   if (plan.use_tma) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err);
   return launch_pass(lc, p, psi, plan.n, m, cl, ptab, btab);

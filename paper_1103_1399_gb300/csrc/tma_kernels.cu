@@ -100,7 +100,10 @@ __host__ __device__ constexpr int tma_c(int q) { return (10 - q) > 3 ? (10 - q) 
 // a2..a2+Q-6 (a2 = a1 + 5 for a contiguous group; a split group, Q = 10 only,
 // takes two 5-bit ranges far apart so that the rows of one tile fall on fewer
 // memory pages).  The tile's fixed bits are [C, a1), [a1+5, a2), [a2+Q-5, n).
-template <int Q, int C, bool WBW>
+// MODE 0: W over the group; 1: W B W (the phase group); 2: the one-qubit
+// rotations of exp(-i theta H_B) on the group's bits (rotation form: B row
+// entries 0..5 = exp(-i theta p)), unnormalised by 2^Q.
+template <int Q, int C, int MODE>
 __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ? 1 : (TmaGeom<Q, C>::NT >= 256 ? 3 : 4)))
     sp_tma_kernel(float2* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, int n, int a1, int a2,
                   const float2* __restrict__ brow, long long ntiles, int* __restrict__ err) {
@@ -128,9 +131,13 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
     mbar_init(s_bar, 1);
     fence_mbar_init();
   }
+  constexpr bool WBW = MODE == 1;
   if (WBW) {
     for (int i = tid; i <= n; i += blockDim.x) s_bt[i] = brow[i];
   }
+  float2 rtab[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) rtab[p] = MODE == 2 ? brow[p] : make_float2(0.f, 0.f);
   __syncthreads();
   if (tid == 0 && static_cast<long long>(blockIdx.x) < ntiles) issue(blockIdx.x);
   const int h_off = j + (th << C);                   // layout H in the dense tile
@@ -155,7 +162,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = src[(r << QB) << C];
     }
-    reg_wht<0, 5>(v);  // i bits QB..QB+4
+    if (MODE == 2) reg_rot<5>(v, rtab); else reg_wht<0, 5>(v);  // i bits QB..QB+4
     if (QB > 0) {
       __syncthreads();  // dense tile fully read
 #pragma unroll
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = s_buf[sx_l + (r << C)];
-      reg_wht<0, QB>(v);  // i bits 0..QB-1
+      if (MODE == 2) reg_rot<QB>(v, rtab); else reg_wht<0, QB>(v);  // i bits 0..QB-1
     }
     if (WBW) {
       // 2^-n exp(-i phi popcount(x)), x the full index
@@ -256,10 +263,13 @@ __device__ __forceinline__ void xpose_y2x_t(float2 (&v)[32], float2* __restrict_
   __syncwarp();
 }
 
+// KIND kLpPhase / kLpRot: the rotation form (P alone; the rotations of bits
+// 0..9 then 2^-n P), with B row entries 0..5 = exp(-i theta p).
 template <int KIND>
 __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     lp_tma_kernel(float2* __restrict__ psi, int m, const ClauseLP* __restrict__ cl, const float2* __restrict__ prow,
-                  long long ntiles, int* __restrict__ err) {
+                  const float2* __restrict__ brow, int n, long long ntiles, int* __restrict__ err) {
+  constexpr bool kRegLow = KIND != kLpFirst && KIND != kLpPhase;  // phase applied in layout Y
   extern __shared__ __align__(1024) unsigned char smem[];
   const LpTmaLayout L(m);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -282,13 +292,18 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     bulk_load(s_buf, psi + (first << kLowBits), 8192u, s_bar);
   }
   for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
-  for (int i = threadIdx.x; i <= m; i += blockDim.x) s_pt[i] = prow[i];
+  // the rotation form's last pass of a step also removes the 2^n of its rotations (exact)
+  const float psc = KIND == kLpRot ? ldexpf(1.0f, -n) : 1.0f;
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) s_pt[i] = make_float2(prow[i].x * psc, prow[i].y * psc);
+  float2 rtab[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) rtab[p] = KIND == kLpRot ? brow[p] : make_float2(0.f, 0.f);
   __syncthreads();
 
   int nconst = 0, npad = 0;
   unsigned pl[kPlanes];
   if (first < ntiles) {
-    fold_tile<KIND != kLpFirst>(s_cl, m, static_cast<unsigned>(first), lane, s_act, nconst, npad);
+    fold_tile<kRegLow>(s_cl, m, static_cast<unsigned>(first), lane, s_act, nconst, npad);
     count_active(s_act, npad, 1u << lane, pl);
   }
   int it = 0;
@@ -305,7 +320,15 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
       for (int r = 0; r < 32; ++r) v[r] = src[32 * r];
     }
     __syncwarp();
-    if (KIND == kLpFirst) {
+    if (KIND == kLpPhase) {
+      apply_p_phase(v, pl, nconst, s_pt);
+    } else if (KIND == kLpRot) {
+      reg_rot<5>(v, rtab);
+      xpose_x2y_t(v, s_buf, lane);
+      reg_rot<5>(v, rtab);
+      apply_p_phase(v, pl, nconst, s_pt);
+      xpose_y2x_t(v, s_buf, lane);
+    } else if (KIND == kLpFirst) {
       apply_p_phase(v, pl, nconst, s_pt);
       reg_wht<0, 5>(v);
       xpose_x2y_t(v, s_buf, lane);
@@ -331,7 +354,7 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     for (int r = 0; r < 32; ++r) g[32 * r] = v[r];
     if (tn < ntiles) {
       __syncwarp();
-      fold_tile<KIND != kLpFirst>(s_cl, m, static_cast<unsigned>(tn), lane, s_act, nconst, npad);
+      fold_tile<kRegLow>(s_cl, m, static_cast<unsigned>(tn), lane, s_act, nconst, npad);
       count_active(s_act, npad, 1u << lane, pl);
     }
   }
@@ -364,7 +387,7 @@ static EncodeTiledFn encode_fn() {
 bool tma_available() { return encode_fn() != nullptr; }
 
 template <int Q, int C>
-static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int a1, int a2, bool wbw,
+static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int a1, int a2, int mode,
                                    const float2* brow, int* err) {
   using G = TmaGeom<Q, C>;
   EncodeTiledFn enc = encode_fn();
@@ -383,7 +406,7 @@ static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int 
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const long long ntiles = 1ll << (n - Q - C);
-  auto kern = wbw ? sp_tma_kernel<Q, C, true> : sp_tma_kernel<Q, C, false>;
+  auto kern = mode == 1 ? sp_tma_kernel<Q, C, 1> : (mode == 2 ? sp_tma_kernel<Q, C, 2> : sp_tma_kernel<Q, C, 0>);
   cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), G::smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -399,17 +422,17 @@ static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int 
 // Contiguous run per tile row: 2^C amplitudes.  C = 4 (128-byte runs) can be
 // requested for groups whose rows lie far apart in memory (see the pass plan).
 template <int Q>
-static cudaError_t launch_sp_tma(const LaunchCtx& lc, float2* psi, int n, int a1, int a2, bool wbw,
+static cudaError_t launch_sp_tma(const LaunchCtx& lc, float2* psi, int n, int a1, int a2, int mode,
                                  const float2* brow, int* err, int c_req) {
   constexpr int C0 = tma_c(Q);
   if (c_req == 4 && C0 < 4 && a1 >= 4)
-    return launch_sp_tma_c<Q, (C0 < 4 ? 4 : C0)>(lc, psi, n, a1, a2, wbw, brow, err);
-  return launch_sp_tma_c<Q, C0>(lc, psi, n, a1, a2, wbw, brow, err);
+    return launch_sp_tma_c<Q, (C0 < 4 ? 4 : C0)>(lc, psi, n, a1, a2, mode, brow, err);
+  return launch_sp_tma_c<Q, C0>(lc, psi, n, a1, a2, mode, brow, err);
 }
 
 template <int KIND>
 static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl,
-                                 const float2* prow, int* err) {
+                                 const float2* prow, const float2* brow, int* err) {
   const long long ntiles = 1ll << (n - kLowBits);
   const LpTmaLayout L(m);
   auto kern = lp_tma_kernel<KIND>;
@@ -422,21 +445,26 @@ static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m,
   long long grid = static_cast<long long>(occ) * lc.num_sms;
   const long long need = (ntiles + kLpTmaWarps - 1) / kLpTmaWarps;
   if (grid > need) grid = need;
-  kern<<<static_cast<unsigned>(grid), kLpTmaWarps * 32, L.total, lc.stream>>>(psi, m, cl, prow, ntiles, err);
+  kern<<<static_cast<unsigned>(grid), kLpTmaWarps * 32, L.total, lc.stream>>>(psi, m, cl, prow, brow, n, ntiles,
+                                                                              err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
                             const float2* ptab, const float2* btab, int* err) {
   const int c_req = p.run_c;
+  const float2* prow = ptab + static_cast<size_t>(p.prow) * (m + 1);
+  const float2* brow = btab + static_cast<size_t>(p.brow) * (n + 1);
   switch (p.kind) {
-    case kLpFirst: return launch_lp_tma<kLpFirst>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), err);
-    case kLpMerge: return launch_lp_tma<kLpMerge>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), err);
-    case kLpLast: return launch_lp_tma<kLpLast>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), err);
+    case kLpFirst: return launch_lp_tma<kLpFirst>(lc, psi, n, m, cl, prow, nullptr, err);
+    case kLpMerge: return launch_lp_tma<kLpMerge>(lc, psi, n, m, cl, prow, nullptr, err);
+    case kLpLast: return launch_lp_tma<kLpLast>(lc, psi, n, m, cl, prow, nullptr, err);
+    case kLpPhase: return launch_lp_tma<kLpPhase>(lc, psi, n, m, cl, prow, nullptr, err);
+    case kLpRot: return launch_lp_tma<kLpRot>(lc, psi, n, m, cl, prow, brow, err);
     case kSpW:
-    case kSpWBW: {
-      const bool wbw = p.kind == kSpWBW;
-      const float2* brow = btab + static_cast<size_t>(p.brow) * (n + 1);
+    case kSpWBW:
+    case kSpRot: {
+      const int wbw = p.kind == kSpWBW ? 1 : (p.kind == kSpRot ? 2 : 0);
       switch (p.q) {
         case 5: return launch_sp_tma<5>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
         case 6: return launch_sp_tma<6>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);

@@ -1,0 +1,51 @@
+"""The 20-qubit configuration's long schedules (T = 40 and T = 160 at dt = 0.05:
+800 and 3200 Strang steps) against stored complex128 oracle results
+(tests/golden/n20_T*.json, written by tests/golden/make_n20_long.py, which
+calls only the oracle).  Checked: the normalised ground-state probability
+(1e-6), <H_P> and <H_B> (1e-4 absolute), the norm drift (5e-6 per 400 steps)
+and the amplitudes at 257 stored indices, the planted solution among them
+(1e-5 absolute, the FP32 bar)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import satgen
+from conftest import GOLDEN
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1103_1399_gb300 as q
+    return q, torch
+
+
+@pytest.mark.parametrize("T", [40, 160])
+@pytest.mark.parametrize("variant", [0, 3], ids=["wbw", "rotation"])
+def test_n20_long_schedule_matches_stored_oracle(env, T, variant):
+    q, torch = env
+    with open(os.path.join(GOLDEN, f"n20_T{T}.json")) as f:
+        g = json.load(f)
+    n, K = g["n"], g["steps"]
+    cl = satgen.load_instance("planted_n20_s0")["clauses"]
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    with q.Instance(n, cl) as inst:
+        inst.set_variant(variant)
+        inst.init_uniform(psi)
+        inst.evolve(psi, g["T"], K)
+        o = inst.observables(psi)
+    idx = torch.as_tensor(g["indices"], device="cuda")
+    got = psi[idx].cpu().numpy().astype(np.complex128)
+    ref = np.array([complex(a, b) for a, b in g["amplitudes"]])
+    assert np.max(np.abs(got - ref)) <= 1e-5
+    assert abs(o["ground_prob"] / o["norm"] - g["success_prob"]) <= 1e-6
+    assert abs(o["norm"] - 1.0) <= 5e-6 * (K / 400)
+    assert abs(o["expect_hp"] - g["expect_hp"]) <= 1e-4
+    assert abs(o["expect_hb"] - g["expect_hb"]) <= 1e-4
+    assert o["ground_count"] == 1

@@ -10,9 +10,11 @@ bench.py times, on outputs the oracle can compute one by one.
   one (two independent routes: the generator's uniqueness proof and the GPU
   count), norm conservation after the 400-step benchmark schedule.
 * Plan invariance: the split-group and contiguous-group pass plans agree.
+* The rotation form (variant 3) on the product instance, same schedule.
 
 Amplitudes at n = 30 are ~2^-15, so the bar is stated relative to the largest
-amplitude of the reference: max |d psi_x| over the sample <= REL_TOL * max |psi_x|.
+amplitude of the reference over all x (closed form for a product state):
+max |d psi_x| over the sample <= REL_TOL * max_x |psi_x|.
 """
 
 import os
@@ -87,6 +89,18 @@ def product_reference(clauses, steps, xs):
     return out
 
 
+def product_max_amplitude(clauses, steps):
+    """The reference's largest |psi_x| over all 2^30 x: the product over qubits of
+    the larger one-qubit amplitude (the bar below is relative to it)."""
+    out = 1.0
+    for i in range(1, N + 1):
+        e0 = sum(1 for c in clauses if c == [i])
+        e1 = sum(1 for c in clauses if c == [-i])
+        f = oracle.one_qubit_strang(e0, e1, DT * steps, steps)
+        out *= max(abs(f[0]), abs(f[1]))
+    return out
+
+
 def product_ground_count(clauses):
     # E(x) = sum_i e_i(x_i) = 0 needs e_i(x_i) = 0 for every i
     count = 1
@@ -105,7 +119,7 @@ def test_product_instance_full_size(env, state):
     xs = rng.integers(0, 1 << N, size=4000)
     ref = product_reference(clauses, K, xs)
     got = gather(torch, state, xs)
-    scale = np.max(np.abs(ref))
+    scale = product_max_amplitude(clauses, K)
     err = np.max(np.abs(got - ref)) / scale
     assert err <= REL_TOL, err
     assert abs(o["norm"] - 1.0) <= NORM_TOL
@@ -154,10 +168,32 @@ def test_pass_plans_agree(env, state):
                 os.environ["QAA_SPLIT_GROUPS"] = old
         results.append(gather(torch, state, xs))
     ref = product_reference(clauses, steps, xs)
-    scale = np.max(np.abs(ref))
+    scale = product_max_amplitude(clauses, steps)
     for got in results:
         assert np.max(np.abs(got - ref)) / scale <= REL_TOL
     assert np.max(np.abs(results[0] - results[1])) / scale <= REL_TOL
+
+
+def test_rotation_form_full_size(env, state):
+    """The rotation form (variant 3) on the full-size product instance, the
+    400-step benchmark schedule: 3 HBM round trips per step."""
+    q, torch = env
+    clauses = product_instance(3)
+    inst = q.Instance(N, clauses)
+    inst.set_variant(3)
+    assert "3 HBM round trips per step" in inst.describe_plan()
+    inst.init_uniform(state)
+    inst.evolve(state, DT * K, K)
+    o = inst.observables(state)
+    inst.close()
+    rng = np.random.default_rng(13)
+    xs = rng.integers(0, 1 << N, size=4000)
+    ref = product_reference(clauses, K, xs)
+    got = gather(torch, state, xs)
+    scale = product_max_amplitude(clauses, K)
+    assert np.max(np.abs(got - ref)) / scale <= REL_TOL
+    assert abs(o["norm"] - 1.0) <= NORM_TOL
+    assert o["ground_count"] == product_ground_count(clauses)
 
 
 def test_plan_description(env):

@@ -101,6 +101,15 @@ def test_graph_tensor_core_variant(env):
     assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("n,K", [(17, 1), (20, 10), (23, 19)])
+def test_graph_rotation_form(env, n, K):
+    q, torch = env
+    cl = satgen.planted_instance(n, 12)["clauses"]
+    a = run(q, torch, n, cl, 0, lambda i, p: i.evolve(p, 0.1 * K, K), variant=3)
+    b = run(q, torch, n, cl, 1, lambda i, p: i.evolve(p, 0.1 * K, K), variant=3)
+    assert torch.equal(a, b)
+
+
 def test_graph_matches_oracle(env):
     q, torch = env
     n, K, T = 16, 25, 2.5

@@ -283,9 +283,51 @@ def test_tensor_core_variant_matches_oracle(q, torch, kind, amp_tol, prob_tol, n
     assert abs(o["ground_prob"] / o["norm"] - oracle.success_prob(ref, e)) <= prob_tol
 
 
+# ------------------------------------------------ rotation form (variant 3) ---
+# exp(-i theta H_B) applied as its n one-qubit factors: the same Strang step as
+# the W B W form, so the same FP32 bar against the oracle.  Cases span every
+# strided width (5..10), two and three strided groups, ragged widths and a
+# sub-range that starts and ends inside the run.
+ROT_CASES = [(15, 3.0, 20), (16, 3.0, 20), (17, 3.0, 12), (18, 2.0, 8), (19, 2.0, 8), (20, 10.0, 200),
+             (21, 1.0, 4), (22, 1.0, 5), (24, 1.0, 3)]
+
+
+@pytest.mark.parametrize("n,T,K", ROT_CASES, ids=[f"n{c[0]}-K{c[2]}" for c in ROT_CASES])
+def test_rotation_form_matches_oracle(q, torch, n, T, K):
+    cl = satgen.load_instance("planted_n20_s0")["clauses"] if n == 20 else satgen.planted_instance(n, 11)["clauses"]
+    e = oracle.violated_counts(n, cl)
+    ref = oracle.evolve_strang(n, cl, T, K, energies=e)
+    inst = q.Instance(n, cl)
+    inst.set_variant(3)
+    assert "rotation form" in inst.describe_plan()
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    inst.init_uniform(psi)
+    inst.evolve(psi, T, K)
+    o = inst.observables(psi)
+    assert np.max(np.abs(to_np(psi) - ref)) <= AMP_TOL
+    assert abs(o["ground_prob"] / o["norm"] - oracle.success_prob(ref, e)) <= PROB_TOL
+    assert abs(o["norm"] - 1.0) <= NORM_TOL
+    inst.close()
+
+
+def test_rotation_form_range_composes(q, torch):
+    n, T, K = 19, 3.0, 30
+    cl = satgen.planted_instance(n, 4)["clauses"]
+    e = oracle.violated_counts(n, cl)
+    ref = oracle.evolve_strang(n, cl, T, K, energies=e)
+    inst = q.Instance(n, cl)
+    inst.set_variant(3)
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    inst.init_uniform(psi)
+    for k0, k1 in ((0, 1), (1, 17), (17, 29), (29, 30)):
+        inst.evolve_range(psi, T, K, k0, k1)
+    assert np.max(np.abs(to_np(psi) - ref)) <= AMP_TOL
+    inst.close()
+
+
 def test_variant_argument_checks(q, torch):
     inst = q.Instance(16, [[1, 2, 3]])
     with pytest.raises(q.QaaError):
-        inst.set_variant(3)
+        inst.set_variant(4)
     with pytest.raises(q.QaaError):
         inst.set_variant(0, 7)
