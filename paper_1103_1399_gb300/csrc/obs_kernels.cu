@@ -5,10 +5,16 @@
 //   norm = sum |psi|^2, <H_P> = sum E |psi|^2, ground = sum_{E=0} |psi|^2,
 //   count of E = 0, and C = sum_i sum_{x: bit i-1 clear} Re(conj psi_x psi_(x+2^(i-1)))
 //   from which <H_B> = n/2 norm - C.
-// Every product is formed in FP64 from the FP32 amplitudes (exact), summed per
-// thread in a fixed order, reduced per block by a fixed shuffle/shared-memory
-// tree into one partial per block and quantity, and the partials are summed by
-// a single block in a fixed order: the result is bit-identical run to run.
+// norm, <H_P> and the ground probability: every product formed in FP64 from
+// the FP32 amplitudes (exact) and summed in FP64.  The pair correlations C
+// (n pair products per amplitude, the bulk of the arithmetic) are formed and
+// summed in FP32 over one thread's share of one tile or column (at most 320
+// products) and accumulated in FP64 beyond that: GB300's FP64 rate is a small
+// fraction of its FP32 rate, and with FP64 pair products the reductions ran at
+// ~2% of the HBM bound.  The FP32 stage adds at most ~320 ulp of the largest
+// product to each partial; independent partials average out in the FP64 sum.
+// Every sum runs in a fixed order (per thread, a fixed shuffle/shared-memory
+// tree per block, the partials by one block): bit-identical run to run.
 #include "device_common.cuh"
 
 namespace qaa {
@@ -103,6 +109,7 @@ __global__ void __launch_bounds__(kObsWarps * 32)
         a_gc += 1.0;
       }
     }
+    float f_corr = 0.f;
     // pairs across register bits (index bits 5..9)
 #pragma unroll
     for (int b = 0; b < 5; ++b) {
@@ -111,8 +118,8 @@ __global__ void __launch_bounds__(kObsWarps * 32)
         for (int r = 0; r < 32; ++r) {
           if (!(r & (1 << b))) {
             const float2 u = v[r], w = v[r | (1 << b)];
-            a_corr = fma(static_cast<double>(u.x), static_cast<double>(w.x), a_corr);
-            a_corr = fma(static_cast<double>(u.y), static_cast<double>(w.y), a_corr);
+            f_corr = fmaf(u.x, w.x, f_corr);
+            f_corr = fmaf(u.y, w.y, f_corr);
           }
         }
       }
@@ -121,18 +128,17 @@ __global__ void __launch_bounds__(kObsWarps * 32)
 #pragma unroll
     for (int b = 0; b < 5; ++b) {
       if (b < n) {
-        const bool lower = !(lane & (1 << b));
+        const float keep = (lane & (1 << b)) ? 0.f : 1.f;  // count each pair once
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
           const float wx = __shfl_xor_sync(0xffffffffu, v[r].x, 1 << b);
           const float wy = __shfl_xor_sync(0xffffffffu, v[r].y, 1 << b);
-          if (lower) {
-            a_corr = fma(static_cast<double>(v[r].x), static_cast<double>(wx), a_corr);
-            a_corr = fma(static_cast<double>(v[r].y), static_cast<double>(wy), a_corr);
-          }
+          f_corr = fmaf(keep * v[r].x, wx, f_corr);
+          f_corr = fmaf(keep * v[r].y, wy, f_corr);
         }
       }
     }
+    a_corr += static_cast<double>(f_corr);
   }
   const double q[kObsQuant] = {a_norm, a_hp, a_gp, a_gc, a_corr};
 #pragma unroll
@@ -156,6 +162,7 @@ __global__ void __launch_bounds__(256)
     float2 v[32];
 #pragma unroll
     for (int r = 0; r < 32; ++r) v[r] = r < (1 << w) ? g[static_cast<unsigned long long>(r) << a] : make_float2(0.f, 0.f);
+    float f = 0.f;  // at most 160 pair products of this column, then FP64
 #pragma unroll
     for (int b = 0; b < 5; ++b) {
       if (b < w) {
@@ -163,12 +170,13 @@ __global__ void __launch_bounds__(256)
         for (int r = 0; r < 32; ++r) {
           if (!(r & (1 << b)) && r < (1 << w)) {
             const float2 u = v[r], z = v[r | (1 << b)];
-            acc = fma(static_cast<double>(u.x), static_cast<double>(z.x), acc);
-            acc = fma(static_cast<double>(u.y), static_cast<double>(z.y), acc);
+            f = fmaf(u.x, z.x, f);
+            f = fmaf(u.y, z.y, f);
           }
         }
       }
     }
+    acc += static_cast<double>(f);
   }
   const double t = block_sum(acc, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;

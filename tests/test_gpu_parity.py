@@ -248,11 +248,14 @@ def test_observables_match_oracle(q, torch, n):
     o = inst.observables(psi)
     assert o["norm"] == pytest.approx(oracle.norm(psi0), rel=1e-12)
     assert o["expect_hp"] == pytest.approx(oracle.expect_hp(psi0, e), rel=1e-12)
-    assert o["expect_hb"] == pytest.approx(oracle.expect_hb(n, psi0), rel=1e-10, abs=1e-9)
+    # norm, <H_P>, ground probability: exact FP64 products, FP64 sums (1e-12).
+    # <H_B>: its pair products are summed in FP32 per thread-tile (<= 320 terms),
+    # then in FP64 -- 1e-7 relative.
+    assert o["expect_hb"] == pytest.approx(oracle.expect_hb(n, psi0), rel=1e-7, abs=1e-9)
     assert o["ground_prob"] == pytest.approx(oracle.success_prob(psi0, e), rel=1e-12, abs=1e-300)
     assert o["ground_count"] == int(np.count_nonzero(e == 0))
     s = 0.37
-    assert inst.energy(psi, s) == pytest.approx(oracle.energy(n, psi0, e, s), rel=1e-10)
+    assert inst.energy(psi, s) == pytest.approx(oracle.energy(n, psi0, e, s), rel=1e-7)
     assert inst.success_prob(psi) == o["ground_prob"]
     assert inst.norm(psi) == o["norm"]
     # fixed reduction order: bit-identical on repeat
