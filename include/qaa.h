@@ -131,7 +131,9 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q);
  * per pass) with every choice of the group that hosts the popcount phase;
  * round 2 toggles the contiguous run per tile row (64 or 128 bytes) of each
  * group of >= 7 bits; round 3 tries recombining two 10-bit groups; round 4
- * plain loads instead of TMA.  Each candidate is timed with CUDA events as the
+ * plain loads instead of TMA; round 5 the rotation form of the H_B factor
+ * (variant 3, see qaa_set_variant) on the best plan so far.  A handle on a
+ * tensor-core variant (1, 2) keeps it and skips round 5.  Each candidate is timed with CUDA events as the
  * best of two runs of `steps` Strang steps (1..64) after one untimed run.
  * Rounds stop once budget_ms of host time is spent (<= 0: 60 s); round 1's
  * first candidate always runs.
@@ -140,9 +142,9 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q);
  *   report   optional (NULL allowed): one line per timed candidate, then the
  *            choice; truncated to len - 1 bytes.
  * The fastest plan becomes this handle's plan and is recorded for n on the
- * current device: every later qaa_create and server request with the same n
- * in this process uses it (unless a QAA_* plan override is set in the
- * environment).  Results of different plans agree within FP32 rounding (the
+ * current device, form included: every later qaa_create and server request
+ * with the same n in this process uses it (unless a QAA_* plan override is set
+ * in the environment); qaa_set_variant still switches a handle's form.  Results of different plans agree within FP32 rounding (the
  * butterfly order differs).  Synchronous.  For n <= 14 there is nothing to
  * tune (QAA_OK, report says so).  The paper has no counterpart.
  */

@@ -406,10 +406,11 @@ namespace {
 
 // One timing of `plan` on the handle: init, `steps` Strang steps (dt = 0.1),
 // the best of two runs, in ms per step; < 0 on a launch error.
-double time_plan(qaa_ctx* h, float2* psi, const qaa::PassPlan& plan, int steps) {
-  const int kind = h->plan.wht_kind;
+// The candidate's own FP32 form (W.B.W or rotation) is timed; a handle on a
+// tensor-core variant keeps that variant.
+double time_plan(qaa_ctx* h, float2* psi, const qaa::PassPlan& plan, int steps, int tc_kind) {
   h->plan = plan;
-  h->plan.wht_kind = kind;
+  if (tc_kind) h->plan.wht_kind = tc_kind;
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
     cudaGetLastError();
@@ -467,10 +468,11 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
   auto spent = [&] {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   };
+  const int tc_kind = (h->plan.wht_kind == 1 || h->plan.wht_kind == 2) ? h->plan.wht_kind : 0;
   qaa::PassPlan best;
   double best_ms = -1.0;
   auto consider = [&](const qaa::PassPlan& cand) {
-    const double ms = time_plan(h, p, cand, steps);
+    const double ms = time_plan(h, p, cand, steps, tc_kind);
     char line[64];
     std::snprintf(line, sizeof line, "%10.4f ms/step  ", ms);
     rep += std::string(line) + qaa::describe_plan(cand) + "\n";
@@ -524,11 +526,16 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
     }
     consider(c);
   }
-  const int kind = h->plan.wht_kind;
+  // round 5: the rotation form of the H_B factor on the best plan (same step,
+  // g instead of 2g - 2 round trips; FP32 CUDA-core passes only)
+  if (!tc_kind && best.use_tma && spent() <= budget_ms) {
+    qaa::PassPlan c = best;
+    c.wht_kind = qaa::kRotationForm;
+    consider(c);
+  }
   h->plan = best;
-  h->plan.wht_kind = kind;
+  if (tc_kind) h->plan.wht_kind = tc_kind;
   qaa::PassPlan rec = best;
-  rec.wht_kind = 0;
   qaa::set_tuned_plan(rec);
   h->prof = prof;
   h->launch_mode = mode;

@@ -326,7 +326,8 @@ cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
   std::vector<qaa::Pass> passes;
   for (long long c0 = 0; e == cudaSuccess && c0 < r->K; c0 += r->chunk) {
     const long long c1 = std::min(r->K, c0 + r->chunk);
-    e = qaa::launch_tables(lc, ptab, btab, r->n, r->m, dt, nullptr, r->K, 0, r->K, c0, c1);
+    e = qaa::launch_tables(lc, ptab, btab, r->n, r->m, dt, nullptr, r->K, 0, r->K, c0, c1,
+                           r->plan.wht_kind == qaa::kRotationForm);
     qaa::build_passes(r->plan, 0, r->K, c0, c1, passes);
     for (const qaa::Pass& ps : passes) {
       if (e != cudaSuccess) break;
