@@ -132,7 +132,8 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q);
  * round 2 toggles the contiguous run per tile row (64 or 128 bytes) of each
  * group of >= 7 bits; round 3 tries recombining two 10-bit groups; round 4
  * plain loads instead of TMA; round 5 the rotation form of the H_B factor
- * (variant 3, see qaa_set_variant) on the best plan so far.  A handle on a
+ * (variant 3, see qaa_set_variant) on the best plan so far, and if it wins,
+ * the run-length toggles of round 2 again.  A handle on a
  * tensor-core variant (1, 2) keeps it and skips round 5.  Each candidate is timed with CUDA events as the
  * best of two runs of `steps` Strang steps (1..64) after one untimed run.
  * Rounds stop once budget_ms of host time is spent (<= 0: 60 s); round 1's

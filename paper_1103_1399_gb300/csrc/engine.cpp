@@ -395,10 +395,15 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (q != 0) return fail(QAA_E_ARG, "only automatic qubits-per-pass (q = 0) is available");
   if (wht_kind == qaa::kRotationForm && h->n > qaa::kOnchipMaxBits && !h->plan.use_tma)
     return fail(QAA_E_ARG, "the rotation form needs the TMA passes (not available, or QAA_PASSES=classic)");
-  // The rotation form keeps the plan's run lengths: measured at n = 30, 128-byte
-  // runs for the split group and 64-byte runs (three CTAs per SM) for the
-  // contiguous one gave 11.36 ms per step, 128-byte runs for both 11.82 ms.
+  qaa::make_plan(h->n, h->plan);
+  const bool tuned_rotation = h->plan.wht_kind == qaa::kRotationForm;  // keep a tuned plan's run lengths
   h->plan.wht_kind = wht_kind;
+  // The rotation form's passes carry more arithmetic than a plain W pass, which
+  // three 64 KiB-tile CTAs per SM hide better than one 128 KiB-tile CTA:
+  // measured at n = 30, 64-byte runs for both groups 10.91 ms per step, the
+  // W.B.W form's choice (128 / 64) 11.22 ms, 128-byte runs for both 11.78 ms.
+  if (wht_kind == qaa::kRotationForm && !tuned_rotation && !std::getenv("QAA_RUN128_GROUPS"))
+    for (int& c : h->plan.run_c) c = 0;
   return QAA_OK;
 }
 
@@ -532,6 +537,15 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
     qaa::PassPlan c = best;
     c.wht_kind = qaa::kRotationForm;
     consider(c);
+    // its passes carry more arithmetic than a plain W pass, so the run lengths
+    // that suit it can differ: toggle them again if it won
+    if (best.wht_kind == qaa::kRotationForm)
+      for (size_t i = 0; i < best.strided.size() && spent() <= budget_ms; ++i) {
+        if (best.strided[i].q < 7) continue;
+        qaa::PassPlan t = best;
+        t.run_c[i] = t.run_c[i] == 4 ? 0 : 4;
+        consider(t);
+      }
   }
   h->plan = best;
   if (tc_kind) h->plan.wht_kind = tc_kind;
