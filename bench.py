@@ -136,6 +136,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, ws, device):
+    """The slowest rank's time: every rank's steps count only once all are done."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, steps, t_max_ms):
+    """Whole-job throughput: every replica evolves its own copy (replicas only,
+    weak scaling), so N ranks complete N x steps Strang steps in the slowest
+    rank's time."""
+    return ws * steps / (t_max_ms / 1e3)
+
+
 # ------------------------------------------------------------- CPU oracle ----
 def oracle_step_sample(n_sample, steps, seed=0):
     """Time the oracle (as it stands) on a planted instance of n_sample variables.
@@ -358,13 +376,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     prof = inst.profile_read()
     inst.profile(False)
-    t_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ws * K / (t_max / 1e3)
+    t_max = max_over_ranks(ms, ws, "cuda")
+    value = job_value(ws, K, t_max)
     obs = inst.observables(psi)
 
     state_bytes = 8 * (1 << n)
