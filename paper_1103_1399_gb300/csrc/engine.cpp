@@ -395,7 +395,7 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (q != 0) return fail(QAA_E_ARG, "only automatic qubits-per-pass (q = 0) is available");
   if (wht_kind == qaa::kRotationForm && h->n > qaa::kOnchipMaxBits && !h->plan.use_tma)
     return fail(QAA_E_ARG, "the rotation form needs the TMA passes (not available, or QAA_PASSES=classic)");
-  qaa::make_plan(h->n, h->plan);
+  qaa::make_plan(h->n, h->plan, (wht_kind == 1 || wht_kind == 2) ? 10 : 11);  // no 11-bit tensor-core tiles
   const bool tuned_rotation = h->plan.wht_kind == qaa::kRotationForm;  // keep a tuned plan's run lengths
   h->plan.wht_kind = wht_kind;
   // The rotation form's passes carry more arithmetic than a plain W pass, which
@@ -507,27 +507,31 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
       c.run_c[i] = c.run_c[i] == 4 ? 0 : 4;
       consider(c);
     }
-  // round 3: two 10-bit groups recombined as {10..14, 25..29} and {15..24}
-  if (best.use_tma && best.strided.size() == 2 && best.strided[0].q == 10 && best.strided[1].q == 10 &&
+  // round 3: two equal q-bit groups (q >= 10) recombined as {10..14, 15+q..} and {15..14+q}, or back
+  if (best.use_tma && best.strided.size() == 2 && best.strided[0].q == best.strided[1].q && best.strided[0].q >= 10 &&
       spent() <= budget_ms) {
     qaa::PassPlan c = best;
+    const int q = c.strided[0].q;
     const bool split = c.strided[0].a2 != c.strided[0].a + 5;
     if (split) {
-      c.strided[0] = {qaa::kLowBits, 10, qaa::kLowBits + 5};
-      c.strided[1] = {qaa::kLowBits + 10, 10, qaa::kLowBits + 15};
+      c.strided[0] = {qaa::kLowBits, q, qaa::kLowBits + 5};
+      c.strided[1] = {qaa::kLowBits + q, q, qaa::kLowBits + q + 5};
     } else {
-      c.strided[0] = {qaa::kLowBits, 10, qaa::kLowBits + 15};
-      c.strided[1] = {qaa::kLowBits + 5, 10, qaa::kLowBits + 10};
+      c.strided[0] = {qaa::kLowBits, q, qaa::kLowBits + q + 5};
+      c.strided[1] = {qaa::kLowBits + 5, q, qaa::kLowBits + 10};
     }
     consider(c);
   }
-  // round 4: plain loads instead of TMA
-  if (best.use_tma && spent() <= budget_ms) {
+  // round 4: plain loads instead of TMA (groups of at most 10 bits, contiguous)
+  bool narrow = true;
+  for (const auto& g : best.strided) narrow = narrow && g.q <= 10;
+  if (best.use_tma && narrow && spent() <= budget_ms) {
     qaa::PassPlan c = best;
     c.use_tma = false;
-    if (c.strided.size() == 2 && c.strided[0].a2 != c.strided[0].a + 5) {  // plain loads need contiguous groups
-      c.strided[0] = {qaa::kLowBits, 10, qaa::kLowBits + 5};
-      c.strided[1] = {qaa::kLowBits + 10, 10, qaa::kLowBits + 15};
+    if (c.strided.size() == 2 && c.strided[0].a2 != c.strided[0].a + 5) {
+      const int q = c.strided[0].q;
+      c.strided[0] = {qaa::kLowBits, q, qaa::kLowBits + 5};
+      c.strided[1] = {qaa::kLowBits + q, q, qaa::kLowBits + q + 5};
     }
     consider(c);
   }

@@ -35,16 +35,18 @@ struct PassPlan {
 
 // Plan for n: the one qaa_autotune chose for n on the current device, if any
 // and if no tuning override is set in the environment; otherwise the default.
-void make_plan(int n, PassPlan& plan);
+// max_q: widest strided group allowed (11 on the TMA FP32 passes; 10 for the
+// plain-load and tensor-core passes, which have no 11-bit tiles).
+void make_plan(int n, PassPlan& plan, int max_q = 11);
 // Default plan for n, with the tuning overrides QAA_PASSES, QAA_SPLIT_GROUPS,
 // QAA_PHASE_GROUP, QAA_RUN128_GROUPS and QAA_GROUP_BITS read from the
 // environment.
-void make_default_plan(int n, PassPlan& plan);
+void make_default_plan(int n, PassPlan& plan, int max_q = 11);
 
 // Autotuner support.  First-round candidates for n >= 15: the default plan,
-// then every split of bits 10..n-1 into the fewest groups of 5..10 bits (the
-// fewest HBM round trips) with every choice of phase group; run lengths 128 B
-// for plain groups and 64 B for the phase group.
+// then every split of bits 10..n-1 into the fewest groups of 5..11 bits (5..10
+// without TMA; the fewest HBM round trips) with every choice of phase group;
+// run lengths 128 B for plain groups and 64 B for the phase group.
 void plan_candidates(int n, std::vector<PassPlan>& out);
 // Contiguous groups of the given widths from bit 10 up.
 void plan_with_groups(int n, const std::vector<int>& sizes, int phase_group, bool tma, PassPlan& plan);

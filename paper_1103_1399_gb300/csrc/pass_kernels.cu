@@ -243,13 +243,13 @@ __device__ __noinline__ float2 p_entry(double dt, const double* s_dev, long long
 }
 
 // With rot set (rotation form) the row instead holds exp(-i dt (1 - s_k) q)
-// unscaled for q = 0..5, the rest zero: the per-block popcount phases of the
-// rotation form's 5-qubit Walsh-Hadamard sandwiches.
+// unscaled for q = 0..6, the rest zero: the per-block popcount phases of the
+// rotation form's 5- and 6-qubit Walsh-Hadamard sandwiches.
 __device__ __noinline__ float2 b_entry(double dt, const double* s_dev, long long K, long long k, int q, double scale,
                                        int rot) {
   const double s = sched_s(s_dev, K, k);
   if (rot) {
-    if (q > 5) return make_float2(0.f, 0.f);
+    if (q > 6) return make_float2(0.f, 0.f);
     scale = 1.0;
   }
   const double ph = dt * (1.0 - s) * static_cast<double>(q);

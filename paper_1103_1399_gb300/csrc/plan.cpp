@@ -106,15 +106,15 @@ bool tuned_plan(int n, PassPlan& out) {
   return true;
 }
 
-// Every split of `rest` bits into g ordered groups of 5..10 bits.
-static void compositions(int rest, int g, std::vector<int>& cur, std::vector<std::vector<int>>& out) {
+// Every split of `rest` bits into g ordered groups of 5..max_q bits.
+static void compositions(int rest, int g, int max_q, std::vector<int>& cur, std::vector<std::vector<int>>& out) {
   if (g == 0) {
     if (rest == 0) out.push_back(cur);
     return;
   }
-  for (int q = 5; q <= 10 && q <= rest; ++q) {
+  for (int q = 5; q <= max_q && q <= rest; ++q) {
     cur.push_back(q);
-    compositions(rest - q, g - 1, cur, out);
+    compositions(rest - q, g - 1, max_q, cur, out);
     cur.pop_back();
   }
 }
@@ -139,11 +139,12 @@ void plan_candidates(int n, std::vector<PassPlan>& out) {
   out.clear();
   if (n <= kOnchipMaxBits) return;
   const int rest = n - kLowBits;
-  const int g = (rest + 9) / 10;
+  const bool tma = tma_available();
+  const int max_q = tma ? 11 : 10;
+  const int g = (rest + max_q - 1) / max_q;
   std::vector<std::vector<int>> comps;
   std::vector<int> cur;
-  compositions(rest, g, cur, comps);
-  const bool tma = tma_available();
+  compositions(rest, g, max_q, cur, comps);
   PassPlan def;
   make_default_plan(n, def);
   out.push_back(def);
@@ -159,18 +160,25 @@ void plan_candidates(int n, std::vector<PassPlan>& out) {
     }
 }
 
-void make_plan(int n, PassPlan& plan) {
-  if (n > kOnchipMaxBits && !env_overrides() && tuned_plan(n, plan)) return;
-  make_default_plan(n, plan);
+static bool fits(const PassPlan& plan, int max_q) {
+  for (const Group& g : plan.strided)
+    if (g.q > max_q) return false;
+  return true;
 }
 
-void make_default_plan(int n, PassPlan& plan) {
+void make_plan(int n, PassPlan& plan, int max_q) {
+  if (n > kOnchipMaxBits && !env_overrides() && tuned_plan(n, plan) && fits(plan, max_q)) return;
+  make_default_plan(n, plan, max_q);
+}
+
+void make_default_plan(int n, PassPlan& plan, int max_q) {
   plan = PassPlan();
   plan.n = n;
   plan.onchip = n <= kOnchipMaxBits;
   const char* env = std::getenv("QAA_PASSES");
   plan.use_tma = tma_available() && !(env && std::strcmp(env, "classic") == 0);
   if (plan.onchip) return;
+  if (!plan.use_tma && max_q > 10) max_q = 10;  // 11-bit groups: TMA FP32 passes only
   const int rest = n - kLowBits;
   std::vector<int> sizes;
   if (const char* gb = std::getenv("QAA_GROUP_BITS")) {
@@ -178,7 +186,7 @@ void make_default_plan(int n, PassPlan& plan) {
     bool ok = true;
     for (const char* p = gb; *p;) {
       const int q = std::atoi(p);
-      if (q < 5 || q > 10) ok = false;
+      if (q < 5 || q > max_q) ok = false;
       sizes.push_back(q);
       sum += q;
       while (*p && *p != ',') ++p;
@@ -187,7 +195,7 @@ void make_default_plan(int n, PassPlan& plan) {
     if (!ok || sum != rest) sizes.clear();
   }
   if (sizes.empty()) {
-    const int ng = (rest + 9) / 10;
+    const int ng = (rest + max_q - 1) / max_q;
     const int base = rest / ng, extra = rest % ng;
     for (int g = 0; g < ng; ++g) sizes.push_back(base + (g < extra ? 1 : 0));
   }
@@ -196,15 +204,17 @@ void make_default_plan(int n, PassPlan& plan) {
     plan.strided.push_back({a, q, a + 5});
     a += q;
   }
-  // Two 10-bit strided groups [10,20) and [20,30): recombine them as
-  // {10..14, 25..29} and {15..24}.  With [20,30) as one group every tile has
-  // 1024 rows 8 MiB apart, each on its own memory page; recombined, a tile
-  // spans at most 128 pages (measured: 6.7 ms -> 3.1 ms per pass at n = 30).
+  // Two equal q-bit strided groups (q = 10 or 11: n = 30, 32), e.g. [10,20)
+  // and [20,30): recombine them as {10..14, 25..29} and {15..24}.  With
+  // [20,30) as one group every tile has 1024 rows 8 MiB apart, each on its own
+  // memory page; recombined, a tile spans at most 128 pages (measured: 6.7 ms
+  // -> 3.1 ms per pass at n = 30).
   const char* sg = std::getenv("QAA_SPLIT_GROUPS");
   const bool split = plan.use_tma && !(sg && std::atoi(sg) == 0);
-  if (split && plan.strided.size() == 2 && plan.strided[0].q == 10 && plan.strided[1].q == 10) {
-    plan.strided[0] = {kLowBits, 10, kLowBits + 15};
-    plan.strided[1] = {kLowBits + 5, 10, kLowBits + 10};
+  if (split && plan.strided.size() == 2 && plan.strided[0].q == plan.strided[1].q && plan.strided[0].q >= 10) {
+    const int q = plan.strided[0].q;
+    plan.strided[0] = {kLowBits, q, kLowBits + q + 5};
+    plan.strided[1] = {kLowBits + 5, q, kLowBits + 10};
   }
   const int ng = static_cast<int>(plan.strided.size());
   plan.phase_group = ng - 1;

@@ -75,7 +75,7 @@ struct LaunchCtx {
 cudaError_t launch_init_uniform(const LaunchCtx& lc, float2* psi, int n);
 // Phase tables for steps c0 <= k < c1 of the range [k0, k1) of a K-step run:
 // c1-c0+1 P rows of m+1 entries and c1-c0 B rows of n+1 entries.
-// rot: B rows in the rotation form's layout (entries q = 0..5 = exp(-i dt (1 - s_k) q), unscaled).
+// rot: B rows in the rotation form's layout (entries q = 0..6 = exp(-i dt (1 - s_k) q), unscaled).
 cudaError_t launch_tables(const LaunchCtx& lc, float2* ptab, float2* btab, int n, int m, double dt,
                           const double* s_dev, long long K, long long k0, long long k1, long long c0, long long c1,
                           bool rot = false);

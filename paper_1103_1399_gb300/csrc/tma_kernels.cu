@@ -99,12 +99,48 @@ struct TmaGeom {
 __host__ __device__ constexpr int tma_c(int q) { return (10 - q) > 3 ? (10 - q) : 3; }
 
 // Active bits: i bits 0..4 sit at index bits a1..a1+4 and i bits 5..Q-1 at
-// a2..a2+Q-6 (a2 = a1 + 5 for a contiguous group; a split group, Q = 10 only,
-// takes two 5-bit ranges far apart so that the rows of one tile fall on fewer
-// memory pages).  The tile's fixed bits are [C, a1), [a1+5, a2), [a2+Q-5, n).
+// a2..a2+Q-6 (a2 = a1 + 5 for a contiguous group; a split group, Q >= 10,
+// takes a 5-bit range and a (Q-5)-bit range far apart so that the rows of one
+// tile fall on fewer memory pages).  The tile's fixed bits are [C, a1),
+// [a1+5, a2), [a2+Q-5, n).  Q = 11 (C = 3, 512 threads): the sixth bit of the
+// layout-L stage is thread bit C, a lane bit, transformed by warp shuffles.
 // MODE 0: W over the group; 1: W B W (the phase group); 2: the one-qubit
 // rotations of exp(-i theta H_B) on the group's bits (rotation form: B row
-// entries 0..5 = exp(-i theta p)), unnormalised by 2^Q.
+// entries 0..6 = exp(-i theta p)), unnormalised by 2^Q.
+//
+// Butterflies over lane bit LB: (u, w) <- (u + w, u - w) across the two lanes.
+template <int LB>
+__device__ __forceinline__ void lane_wht(float2 (&v)[32], int lane) {
+  const bool upper = (lane >> LB) & 1;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const float px = __shfl_xor_sync(0xffffffffu, v[r].x, 1 << LB);
+    const float py = __shfl_xor_sync(0xffffffffu, v[r].y, 1 << LB);
+    v[r] = upper ? make_float2(px - v[r].x, py - v[r].y) : make_float2(v[r].x + px, v[r].y + py);
+  }
+}
+
+// Layout-L stage over i bits 0..QB-1: registers hold i bits 0..4, a sixth bit
+// (QB = 6) is lane bit C.  MODE 2 applies the rotation-form sandwich over all
+// QB bits (its popcount counts the lane bit too).
+template <int QB, int C, int MODE>
+__device__ __forceinline__ void stage_l(float2 (&v)[32], const float2 (&rtab)[7], int lane) {
+  if constexpr (QB <= 5) {
+    if (MODE == 2) reg_rot<QB>(v, *reinterpret_cast<const float2(*)[6]>(&rtab)); else reg_wht<0, QB>(v);
+  } else {
+    static_assert(QB == 6 && C < 5, "a sixth layout-L bit must be a lane bit");
+    reg_wht<0, 5>(v);
+    lane_wht<C>(v, lane);
+    if (MODE == 2) {
+      const int hb = (lane >> C) & 1;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = cmul(v[r], rtab[__builtin_popcount(r) + hb]);
+      reg_wht<0, 5>(v);
+      lane_wht<C>(v, lane);
+    }
+  }
+}
+
 template <int Q, int C, int MODE>
 __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ? 1 : (TmaGeom<Q, C>::NT >= 256 ? 3 : 4)))
     sp_tma_kernel(float2* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, int n, int a1, int a2,
@@ -137,9 +173,10 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
   if (WBW) {
     for (int i = tid; i <= n; i += blockDim.x) s_bt[i] = brow[i];
   }
-  float2 rtab[6];
+  float2 rtab[7];
 #pragma unroll
-  for (int p = 0; p < 6; ++p) rtab[p] = MODE == 2 ? brow[p] : make_float2(0.f, 0.f);
+  for (int p = 0; p < 7; ++p) rtab[p] = MODE == 2 ? brow[p] : make_float2(0.f, 0.f);
+  const int lane = tid & 31;
   __syncthreads();
   if (tid == 0 && static_cast<long long>(blockIdx.x) < ntiles) issue(blockIdx.x);
   const int h_off = j + (th << C);                   // layout H in the dense tile
@@ -164,7 +201,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = src[(r << QB) << C];
     }
-    if (MODE == 2) reg_rot<5>(v, rtab); else reg_wht<0, 5>(v);  // i bits QB..QB+4
+    if (MODE == 2) reg_rot<5>(v, *reinterpret_cast<const float2(*)[6]>(&rtab)); else reg_wht<0, 5>(v);  // i bits QB..QB+4
     if (QB > 0) {
       __syncthreads();  // dense tile fully read
 #pragma unroll
@@ -172,7 +209,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = s_buf[sx_l + (r << C)];
-      if (MODE == 2) reg_rot<QB>(v, rtab); else reg_wht<0, QB>(v);  // i bits 0..QB-1
+      stage_l<QB, C, MODE>(v, rtab, lane);  // i bits 0..QB-1
     }
     if (WBW) {
       // 2^-n exp(-i phi popcount(x)), x the full index
@@ -180,7 +217,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = cmul(v[r], s_bt[pc0 + __popc(r)]);
       if (QB > 0) {
-        reg_wht<0, QB>(v);
+        stage_l<QB, C, 0>(v, rtab, lane);
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 32; ++r) s_buf[sx_l + (r << C)] = v[r];
@@ -200,8 +237,9 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
       }
     }
     if (WBW || QB == 0) {
-      // layout H: i = th + (r << QB); th = i bits 0..QB-1 lie at a1..
-      float2* dst = psi + xbase + j + (static_cast<unsigned long long>(th) << a1);
+      // layout H: i = th + (r << QB); th = i bits 0..QB-1: bits 0..4 lie at a1.., bit 5 (QB = 6) at a2
+      float2* dst = psi + xbase + j + (static_cast<unsigned long long>(th & 31) << a1) +
+                    (static_cast<unsigned long long>(th >> 5) << a2);
 #pragma unroll
       for (int r = 0; r < 32; ++r) {
         *dst = v[r];
@@ -413,7 +451,7 @@ static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int 
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   constexpr int QB = Q - 5;
-  if (a1 < C || a2 < a1 + 5 || a2 + QB > n || (a2 != a1 + 5 && QB != 5)) return cudaErrorInvalidValue;
+  if (a1 < C || a2 < a1 + 5 || a2 + QB > n || (a2 != a1 + 5 && QB < 5)) return cudaErrorInvalidValue;
   CUtensorMap map;
   // dims (innermost first): bits [0,a1), [a1,a1+5), [a1+5,a2), [a2,a2+QB), [a2+QB,n)
   const cuuint64_t dims[5] = {1ull << a1, 32ull, 1ull << (a2 - a1 - 5), 1ull << QB, 1ull << (n - a2 - QB)};
@@ -445,8 +483,10 @@ template <int Q>
 static cudaError_t launch_sp_tma(const LaunchCtx& lc, float2* psi, int n, int a1, int a2, int mode,
                                  const float2* brow, int* err, int c_req) {
   constexpr int C0 = tma_c(Q);
-  if (c_req == 4 && C0 < 4 && a1 >= 4)
-    return launch_sp_tma_c<Q, (C0 < 4 ? 4 : C0)>(lc, psi, n, a1, a2, mode, brow, err);
+  if constexpr (Q <= 10) {  // an 11-bit tile with 128-byte runs would not fit in shared memory
+    if (c_req == 4 && C0 < 4 && a1 >= 4)
+      return launch_sp_tma_c<Q, (C0 < 4 ? 4 : C0)>(lc, psi, n, a1, a2, mode, brow, err);
+  }
   return launch_sp_tma_c<Q, C0>(lc, psi, n, a1, a2, mode, brow, err);
 }
 
@@ -492,6 +532,7 @@ cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int
         case 8: return launch_sp_tma<8>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
         case 9: return launch_sp_tma<9>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
         case 10: return launch_sp_tma<10>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
+        case 11: return launch_sp_tma<11>(lc, psi, n, p.a, p.a2, wbw, brow, err, c_req);
         default: return cudaErrorInvalidValue;
       }
     }

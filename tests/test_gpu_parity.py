@@ -133,7 +133,7 @@ EVOLVE_CASES = [
     (18, "planted", 2.0, 8),      # width 8
     (19, "planted", 2.0, 8),      # width 9
     (20, "planted20", 10.0, 200), # the n=20 configuration, T=10, dt=0.05
-    (21, "planted", 1.0, 4),      # three groups (6, 5)
+    (21, "planted", 1.0, 4),      # one 11-bit strided group (2 round trips per step)
 ]
 
 
