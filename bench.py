@@ -19,6 +19,7 @@ whole-job steps/s = N K / max-over-ranks time.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -245,6 +246,70 @@ def serving_workload(count, seed=0):
 def _pct(v, p):
     import numpy as np
     return float(np.percentile(np.asarray(v), p)) if v else None
+
+
+def small_configs(q, torch, stream):
+    """n = 12: ten planted instances (seeds 0..9), T = 20, 400 steps, solved one at
+    a time through the handle API (the on-chip evolver): solves/s, P_succ, norm.
+    n = 20 (the committed instance): T = 10, 40, 160 (200, 800, 3200 steps):
+    steps/s and the L2 bandwidth of its 2 round trips per step (the state fits
+    in L2)."""
+    import satgen
+    out = {}
+    ps, norms = [], []
+    psi = torch.empty(1 << 12, dtype=torch.complex64, device="cuda")
+    insts = [satgen.planted_instance(12, s)["clauses"] for s in range(10)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for cl in insts:
+        with q.Instance(12, cl, stream=stream) as inst:
+            inst.init_uniform(psi)
+            inst.evolve(psi, 20.0, 400)
+            o = inst.observables(psi)
+        ps.append(o["ground_prob"] / o["norm"])
+        norms.append(o["norm"])
+    wall = time.perf_counter() - t0
+    out["n12"] = {"solves_per_s": len(insts) / wall, "steps": 400, "T": 20.0, "seeds": "0..9",
+                  "p_succ": ps, "norm_minus_1_max": max(abs(x - 1.0) for x in norms),
+                  "what": "qaa_create + init + evolve + observables per instance, host-timed"}
+    cl20 = satgen.load_instance("planted_n20_s0")["clauses"]
+    p20 = torch.empty(1 << 20, dtype=torch.complex64, device="cuda")
+    rows = []
+    with q.Instance(20, cl20, stream=stream) as inst:
+        inst.init_uniform(p20)
+        inst.evolve(p20, 1.0, 20)  # warm-up
+        rts = 2 * inst.describe_plan().count("group bits")
+        for T in (10.0, 40.0, 160.0):
+            K = int(round(T / 0.05))
+            inst.init_uniform(p20)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inst.evolve(p20, T, K)
+            e1.record(stream)
+            o = inst.observables(p20)
+            ms = e0.elapsed_time(e1)
+            rows.append({"T": T, "steps": K, "steps_per_s": K / (ms / 1e3),
+                         "l2_gbs": rts * 2 * 8 * (1 << 20) * K / (ms / 1e3) / 1e9,
+                         "p_succ": o["ground_prob"] / o["norm"], "norm": o["norm"]})
+    out["n20"] = {"plan": f"{rts} round trips per step", "runs": rows}
+    # random 3-SAT at ratio 4.2 (degenerate ground state), sin^2 schedule
+    rd = satgen.ratio_instance(20, 1, min_solutions=2)
+    K, T = 800, 40.0
+    s_values = [math.sin(0.5 * math.pi * (k + 0.5) / K) ** 2 for k in range(K)]
+    with q.Instance(20, rd["clauses"], stream=stream) as inst:
+        inst.init_uniform(p20)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inst.evolve_schedule(p20, T / K, s_values)
+        e1.record(stream)
+        o = inst.observables(p20)
+        ms = e0.elapsed_time(e1)
+    out["ratio42_n20"] = {"m": rd["m"], "solutions": rd["solutions"], "ground_count": o["ground_count"],
+                          "schedule": "s(t) = sin^2(pi t / 2T)", "T": T, "steps": K,
+                          "steps_per_s": K / (ms / 1e3), "p_succ": o["ground_prob"] / o["norm"]}
+    return out
 
 
 def autotune_sizes(q, torch, work):
@@ -481,6 +546,12 @@ def run_ours(args):
         torch.cuda.empty_cache()
         psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
 
+    # the small configurations: n = 12 (T = 20, seeds 0..9, on chip) and n = 20
+    # (T = 10, 40, 160; the 8 MiB state is L2-resident), dt = 0.05
+    small = None
+    if not args.no_small and rank == 0:
+        small = small_configs(q, torch, stream)
+
     # e2e: a full solve through the public API with the instance in host memory
     e2e = None
     if not args.no_e2e:
@@ -532,6 +603,7 @@ def run_ours(args):
             "e2e": e2e,
             "precision_variants": variants,
             "launch_graph": graph,
+            "small_configs": small,
             "n32": n32,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -555,6 +627,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip timing the tensor-core WHT variants and the launch-graph mode")
     ap.add_argument("--no-n32", action="store_true", help="skip the short 32-qubit (32 GiB) run")
+    ap.add_argument("--no-small", action="store_true", help="skip the n=12 and n=20 configuration lines")
     ap.add_argument("--serving-requests", type=int, default=1024,
                     help="requests in the batched-serving measurement (0 skips it)")
     ap.add_argument("--instance", default=INSTANCE,

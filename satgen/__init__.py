@@ -143,6 +143,48 @@ def random_instance(n, m, seed, width=3):
     return out
 
 
+def count_solutions(n, clauses, chunk_bits=22):
+    """Number of assignments satisfying every clause (brute force, n <= 26)."""
+    if n > 26:
+        raise ValueError("brute-force counting is for n <= 26")
+    total = 0
+    chunk = 1 << min(chunk_bits, n)
+    for base in range(0, 1 << n, chunk):
+        alive = np.arange(base, base + chunk, dtype=np.int64)
+        for lits in clauses:
+            alive = alive[_satisfied(alive, lits)]
+            if alive.size == 0:
+                break
+        total += int(alive.size)
+    return total
+
+
+def ratio_instance(n, seed, ratio=4.2, min_solutions=1):
+    """Uniform random 3-SAT at a clause/variable ratio (Sec. 4.3 uses ~4.2,
+    near the satisfiability threshold; those instances were never published).
+
+    ``rng = default_rng(seed)``; m = round(ratio * n) clauses, each three distinct
+    variables ``rng.choice(n, 3, replace=False)`` and signs ``rng.integers(0, 2,
+    3)``, repeats allowed; no planted solution, so the ground state may be
+    degenerate.  Instances with fewer than ``min_solutions`` satisfying
+    assignments are redrawn from the same generator (deterministic per seed).
+    Returns a dict with keys n, seed, m, clauses, solutions, draws.
+    """
+    rng = np.random.default_rng(seed)
+    m = int(round(ratio * n))
+    for draw in range(1, 10001):
+        clauses = []
+        for _ in range(m):
+            vs = rng.choice(n, size=3, replace=False)
+            signs = rng.integers(0, 2, size=3)
+            clauses.append([int(v) + 1 if sg else -(int(v) + 1) for v, sg in zip(vs, signs)])
+        sols = count_solutions(n, clauses)
+        if sols >= min_solutions:
+            return {"n": n, "seed": seed, "m": m, "clauses": clauses, "solutions": sols, "draws": draw,
+                    "generator": f"satgen random 3-SAT ratio {ratio:g} v1"}
+    raise RuntimeError("no instance with enough solutions in 10000 draws")
+
+
 def save_instance(inst, path):
     with open(path, "w") as f:
         json.dump(inst, f, separators=(",", ":"))

@@ -49,3 +49,25 @@ def test_n20_long_schedule_matches_stored_oracle(env, T, variant):
     assert abs(o["expect_hp"] - g["expect_hp"]) <= 1e-4
     assert abs(o["expect_hb"] - g["expect_hb"]) <= 1e-4
     assert o["ground_count"] == 1
+
+
+def test_n20_adiabatic_trend(env):
+    """The 20-qubit configuration's schedules T = 10, 40, 160: the ground-state
+    probability grows with T and ends above 0.9 (Sec. 2.1: the evolution stays
+    in the ground state when slow enough); T = 40 and 160 also match the
+    stored oracle values."""
+    q, torch = env
+    cl = satgen.load_instance("planted_n20_s0")["clauses"]
+    psi = torch.empty(1 << 20, dtype=torch.complex64, device="cuda")
+    probs = {}
+    with q.Instance(20, cl) as inst:
+        for T in (10, 40, 160):
+            inst.init_uniform(psi)
+            inst.evolve(psi, float(T), int(round(T / 0.05)))
+            o = inst.observables(psi)
+            probs[T] = o["ground_prob"] / o["norm"]
+    assert probs[10] < probs[40] < probs[160]
+    assert probs[160] > 0.9
+    for T in (40, 160):
+        with open(os.path.join(GOLDEN, f"n20_T{T}.json")) as f:
+            assert abs(probs[T] - json.load(f)["success_prob"]) <= 1e-6

@@ -47,3 +47,19 @@ def test_serving_requests_shape():
     arr = [r[0] for r in reqs]
     assert arr == sorted(arr)
     assert all(10 <= r[1] <= 22 and 5.0 <= r[2] <= 80.0 for r in reqs)
+
+
+def test_count_solutions_matches_brute_force_energies():
+    import oracle
+    for n, seed in ((6, 1), (9, 2), (12, 3)):
+        cl = satgen.random_instance(n, int(4.2 * n), seed)
+        assert satgen.count_solutions(n, cl) == int(np.count_nonzero(oracle.violated_counts(n, cl) == 0))
+
+
+def test_ratio_instance_is_deterministic_and_degenerate_when_asked():
+    a = satgen.ratio_instance(14, 5, min_solutions=2)
+    b = satgen.ratio_instance(14, 5, min_solutions=2)
+    assert a["clauses"] == b["clauses"] and a["m"] == round(4.2 * 14)
+    assert a["solutions"] >= 2
+    assert all(len(set(abs(l) for l in c)) == 3 for c in a["clauses"])
+    assert satgen.count_solutions(14, a["clauses"]) == a["solutions"]
