@@ -46,6 +46,11 @@ from .evolve import (
     expect_hb,
     energy,
     one_qubit_strang,
+    evolve_substeps,
+    order4_substeps,
+    evolve_order4,
+    YOSHIDA_W0,
+    YOSHIDA_W1,
 )
 
 __all__ = [

@@ -166,3 +166,54 @@ def test_product_instance_factorises():
         for i in range(n):
             amp *= factors[i][(x >> i) & 1]
         assert abs(amp - psi[x]) < 1e-12
+
+
+# ---------------------------------------------------------- fourth order ----
+def test_yoshida_weights():
+    w1, w0 = oracle.YOSHIDA_W1, oracle.YOSHIDA_W0
+    assert abs(2 * w1 + w0 - 1.0) < 1e-15           # consistency
+    assert abs(2 * w1 ** 3 + w0 ** 3) < 1e-14       # third-order error cancels
+    assert w0 < 0 < w1
+
+
+def test_substeps_with_equal_lengths_equal_strang():
+    inst = satgen.planted_instance(6, 2)
+    n, cl, T, K = 6, inst["clauses"], 3.0, 17
+    s = oracle.midpoint_schedule(K)
+    a = oracle.evolve_substeps(n, cl, np.full(K, T / K), s)
+    b = oracle.evolve_strang(n, cl, T, K)
+    assert np.max(np.abs(a - b)) < 1e-14
+
+
+def test_order4_substeps_tile_the_interval():
+    T, K = 2.5, 7
+    dts, ss = oracle.order4_substeps(T, K)
+    assert dts.shape == ss.shape == (3 * K,)
+    assert abs(dts.sum() - T) < 1e-13
+    # every sub-step's s is the midpoint of its own time interval
+    t = np.concatenate([[0.0], np.cumsum(dts)])
+    assert np.allclose(ss, 0.5 * (t[:-1] + t[1:]) / T, atol=1e-15)
+
+
+def test_order4_converges_at_fourth_order_frozen_rabi():
+    s, T = 0.4, 5.0
+    ref = rabi_closed_form(s, T, PSI0_1Q)
+    errs = []
+    for K in (10, 20, 40):
+        dts, _ = oracle.order4_substeps(T, K)
+        got = oracle.evolve_substeps(1, [[1]], dts, np.full(3 * K, s), psi0=PSI0_1Q)
+        errs.append(np.max(np.abs(got - ref)))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(14.0 < r < 18.0 for r in ratios), ratios
+
+
+def test_order4_converges_at_fourth_order_time_dependent_sat():
+    # linear schedule (H depends on t): reference = fourth order at 8x the steps
+    inst = satgen.planted_instance(6, 3)
+    n, cl, T = 6, inst["clauses"], 4.0
+    ref = oracle.evolve_order4(n, cl, T, 320)
+    errs = [np.max(np.abs(oracle.evolve_order4(n, cl, T, K) - ref)) for K in (20, 40)]
+    assert 13.0 < errs[0] / errs[1] < 19.0, errs
+    # and it beats Strang at equal work (3 Strang sub-steps per fourth-order step)
+    strang = np.max(np.abs(oracle.evolve_strang(n, cl, T, 120) - ref))
+    assert errs[1] < strang
