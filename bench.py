@@ -507,6 +507,24 @@ def run_ours(args):
                          "WHILE loop over 8-step bodies"}
         gi.close()
 
+    # fourth-order steps (Yoshida triple jump: 3 Strang sub-steps each) on the same workload
+    order4 = None
+    if not args.no_variants:
+        oi = q.Instance(n, clauses, stream=stream)
+        ok4 = 30
+        oi.init_uniform(psi)
+        oi.evolve_order4(psi, DT * 3, 3)
+        torch.cuda.synchronize()
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        oi.evolve_order4(psi, DT * ok4, ok4)
+        o1.record(stream)
+        torch.cuda.synchronize()
+        oms = o0.elapsed_time(o1)
+        order4 = {"steps_per_s": ok4 / (oms / 1e3), "substeps_per_s": 3 * ok4 / (oms / 1e3), "steps": ok4,
+                  "what": "qaa_evolve_order4: each step of dt = 0.1 is three Strang sub-steps (Yoshida weights)"}
+        oi.close()
+
     # the 32-qubit case of the same configuration (32 GiB state), a short run
     n32 = None
     if not args.no_n32 and rank == 0:
@@ -603,6 +621,7 @@ def run_ours(args):
             "e2e": e2e,
             "precision_variants": variants,
             "launch_graph": graph,
+            "order4": order4,
             "small_configs": small,
             "n32": n32,
             "serving": serving,

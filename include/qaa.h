@@ -190,6 +190,29 @@ int qaa_evolve_range(qaa_handle h, void* psi, double T, int64_t steps, int64_t k
 int qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_values, int64_t steps);
 
 /*
+ * qaa_evolve_substeps -- `count` Strang sub-steps of individual length:
+ * sub-step j has length dt_values[j] (any finite real, negative = backwards in
+ * time) with H frozen at s = s_values[j] (host arrays of `count` doubles,
+ * copied before return).  Adjacent half phases are merged with their own
+ * lengths: exp(-i (dt_j s_j + dt_(j+1) s_(j+1))/2 H_P).  Equal lengths give
+ * exactly qaa_evolve_schedule.  Asynchronous on the handle's stream.
+ * QAA_E_ARG for null arrays, count < 1 or a non-finite entry.
+ */
+int qaa_evolve_substeps(qaa_handle h, void* psi, const double* dt_values, const double* s_values, int64_t count);
+
+/*
+ * qaa_evolve_order4 -- the linear schedule s = t/T of Eq. (1) in `steps`
+ * fourth-order steps: each step of length dt = T/steps is Yoshida's triple
+ * jump (Phys. Lett. A 150, 262 (1990)) of Strang sub-steps w1 dt, w0 dt, w1 dt
+ * with w1 = 1/(2 - 2^(1/3)), w0 = 1 - 2 w1 (< 0), each frozen at s of its own
+ * midpoint time; 3 x steps sub-steps through qaa_evolve_substeps.  The error
+ * falls as dt^4 instead of dt^2 (the paper names no integrator; this is a
+ * higher-order alternative to the Strang split of qaa_evolve).
+ * QAA_E_ARG for T < 0 or not finite, steps outside [1, 2^28].
+ */
+int qaa_evolve_order4(qaa_handle h, void* psi, double T, int64_t steps);
+
+/*
  * Observables, accumulated in FP64 from the complex64 state with a fixed
  * two-level reduction order (bit-identical run to run).  Synchronous.
  *   norm         sum_x |psi_x|^2

@@ -55,6 +55,9 @@ SIGNATURES = {
     "qaa_set_stream": (_c_int, [_vp, _vp]),
     "qaa_set_variant": (_c_int, [_vp, _c_int, _c_int]),
     "qaa_set_launch_mode": (_c_int, [_vp, _c_int]),
+    "qaa_evolve_substeps": (_c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.c_int64]),
+    "qaa_evolve_order4": (_c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int64]),
     "qaa_autotune": (_c_int, [_vp, _vp, _c_int, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
     "qaa_tune_candidates": (_c_int, [_c_int, ctypes.c_char_p, ctypes.c_size_t]),
     "qaa_forget_tuned_plans": (_c_int, []),
@@ -224,6 +227,22 @@ class Instance:
         s = [float(v) for v in s_values]
         arr = (ctypes.c_double * len(s))(*s)
         _check(lib.qaa_evolve_schedule(self._h, _ptr(psi), float(dt), arr, len(s)))
+
+    def evolve_substeps(self, psi, dt_values, s_values):
+        """Strang sub-steps of individual lengths dt_values[j], frozen at s_values[j] (qaa_evolve_substeps)."""
+        _check_state(self, psi)
+        d = [float(v) for v in dt_values]
+        s = [float(v) for v in s_values]
+        if len(d) != len(s):
+            raise ValueError("dt_values and s_values must have the same length")
+        da = (ctypes.c_double * len(d))(*d)
+        sa = (ctypes.c_double * len(s))(*s)
+        _check(lib.qaa_evolve_substeps(self._h, _ptr(psi), da, sa, len(d)))
+
+    def evolve_order4(self, psi, T, steps):
+        """The linear schedule in fourth-order (Yoshida triple-jump) steps (qaa_evolve_order4)."""
+        _check_state(self, psi)
+        _check(lib.qaa_evolve_order4(self._h, _ptr(psi), float(T), int(steps)))
 
     def observables(self, psi):
         _check_state(self, psi)

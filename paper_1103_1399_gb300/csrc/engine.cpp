@@ -61,11 +61,13 @@ struct qaa_ctx {
     const void* psi;
     double dt;
     const double* s_dev;
+    const double* dt_dev;
     long long K, k0, k1;
     int wht_kind;
     cudaStream_t stream;
     bool operator==(const GraphKey& o) const {
-      return psi == o.psi && std::memcmp(&dt, &o.dt, sizeof dt) == 0 && s_dev == o.s_dev && K == o.K && k0 == o.k0 &&
+      return psi == o.psi && std::memcmp(&dt, &o.dt, sizeof dt) == 0 && s_dev == o.s_dev && dt_dev == o.dt_dev &&
+             K == o.K && k0 == o.k0 &&
              k1 == o.k1 && wht_kind == o.wht_kind && stream == o.stream;
     }
   } gkey{};
@@ -181,14 +183,15 @@ int prof_kind(int pass_kind) {
 // Streaming plan, launch-graph mode: build (or reuse) the graph of the whole
 // range and launch it.  The graph is rebuilt when psi, the schedule, the range,
 // the variant or the stream changes.
-int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, long long k1, const double* s_dev) {
+int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, long long k1, const double* s_dev,
+                 const double* dt_dev) {
   if (!h->d_gscratch) {
     if (cudaMalloc(&h->d_gscratch, qaa::graph_scratch_bytes(h->n, h->m)) != cudaSuccess) {
       cudaGetLastError();
       return fail(QAA_E_NOMEM, "cannot allocate graph scratch");
     }
   }
-  const qaa_ctx::GraphKey key{psi, dt, s_dev, K, k0, k1, h->plan.wht_kind, h->stream};
+  const qaa_ctx::GraphKey key{psi, dt, s_dev, dt_dev, K, k0, k1, h->plan.wht_kind, h->stream};
   if (!h->gexec || !(key == h->gkey)) {
     if (h->gexec) {
       QAA_CK(cudaStreamSynchronize(h->stream));
@@ -203,6 +206,7 @@ int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, 
     gs.err = h->d_err;
     gs.dt = dt;
     gs.s_dev = s_dev;
+    gs.dt_dev = dt_dev;
     gs.K = K;
     gs.k0 = k0;
     gs.k1 = k1;
@@ -215,7 +219,10 @@ int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, 
   return QAA_OK;
 }
 
-int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, long long k1, const double* s_host) {
+// s_host / dt_host (K entries each, optional): the caller's schedule and per-step
+// lengths, copied to the device ahead of the launches on the handle's stream.
+int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, long long k1, const double* s_host,
+                const double* dt_host = nullptr) {
   int st = check_handle(h);
   if (st) return st;
   if (!psi) return fail(QAA_E_ARG, "psi is null");
@@ -224,8 +231,9 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
   if (!std::isfinite(dt)) return fail(QAA_E_ARG, "dt must be finite");
   if (k0 == k1) return QAA_OK;
   const double* s_dev = nullptr;
-  if (s_host) {
-    const size_t need = static_cast<size_t>(K);
+  const double* dt_dev = nullptr;
+  if (s_host || dt_host) {
+    const size_t need = static_cast<size_t>(K) * 2;  // [0, K): s, [K, 2K): dt
     if (need > h->s_cap) {
       if (h->d_s) {
         QAA_CK(cudaStreamSynchronize(h->stream));
@@ -239,11 +247,17 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
       }
       h->s_cap = need;
     }
-    QAA_CK(cudaMemcpyAsync(h->d_s, s_host, need * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    s_dev = h->d_s;
+    if (s_host) {
+      QAA_CK(cudaMemcpyAsync(h->d_s, s_host, K * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      s_dev = h->d_s;
+    }
+    if (dt_host) {
+      QAA_CK(cudaMemcpyAsync(h->d_s + K, dt_host, K * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      dt_dev = h->d_s + K;
+    }
   }
   if (h->launch_mode == QAA_LAUNCH_GRAPH && h->n > qaa::kOnchipMaxBits)
-    return evolve_graph(h, static_cast<float2*>(psi), dt, K, k0, k1, s_dev);
+    return evolve_graph(h, static_cast<float2*>(psi), dt, K, k0, k1, s_dev, dt_dev);
   const long long chunk = std::min(kChunkSteps, k1 - k0);
   const size_t prow = static_cast<size_t>(h->m + 1), brow = static_cast<size_t>(h->n + 1);
   st = ensure_tab(h, static_cast<size_t>(chunk + 1) * prow + static_cast<size_t>(chunk) * brow);
@@ -257,7 +271,7 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
     const long long c1 = std::min(k1, c0 + chunk);
     QAA_CK(timed(h, QAA_K_TABLES, [&] {
       return qaa::launch_tables(lc, ptab, btab, h->n, h->m, dt, s_dev, K, k0, k1, c0, c1,
-                                h->n > qaa::kOnchipMaxBits && h->plan.wht_kind == qaa::kRotationForm);
+                                h->n > qaa::kOnchipMaxBits && h->plan.wht_kind == qaa::kRotationForm, dt_dev);
     }));
     if (h->n <= qaa::kOnchipMaxBits) {
       QAA_CK(timed(h, QAA_K_ONCHIP, [&] {
@@ -607,6 +621,35 @@ int qaa_evolve_range(qaa_handle h, void* psi, double T, int64_t steps, int64_t k
   if (!(T >= 0.0) || !std::isfinite(T)) return fail(QAA_E_ARG, "T must be finite and >= 0");
   if (steps < 1) return fail(QAA_E_ARG, "steps must be >= 1");
   return evolve_impl(h, psi, T / static_cast<double>(steps), steps, k0, k1, nullptr);
+}
+
+int qaa_evolve_substeps(qaa_handle h, void* psi, const double* dt_values, const double* s_values, int64_t count) {
+  if (!dt_values || !s_values) return fail(QAA_E_ARG, "dt_values or s_values is null");
+  if (count < 1) return fail(QAA_E_ARG, "count must be >= 1");
+  for (int64_t k = 0; k < count; ++k)
+    if (!std::isfinite(dt_values[k]) || !std::isfinite(s_values[k]))
+      return fail(QAA_E_ARG, "dt_values and s_values must be finite");
+  return evolve_impl(h, psi, 0.0, count, 0, count, s_values, dt_values);
+}
+
+int qaa_evolve_order4(qaa_handle h, void* psi, double T, int64_t steps) {
+  if (!(T >= 0.0) || !std::isfinite(T)) return fail(QAA_E_ARG, "T must be finite and >= 0");
+  if (steps < 1 || steps > (1ll << 28)) return fail(QAA_E_ARG, "steps must be in [1, 2^28]");
+  // Yoshida's triple jump: weights w1, w0, w1 with 2 w1 + w0 = 1, 2 w1^3 + w0^3 = 0
+  const double w1 = 1.0 / (2.0 - std::cbrt(2.0)), w0 = 1.0 - 2.0 * w1;
+  const double w[3] = {w1, w0, w1};
+  const double dt = T / static_cast<double>(steps);
+  std::vector<double> dts(static_cast<size_t>(3 * steps)), ss(static_cast<size_t>(3 * steps));
+  for (int64_t k = 0; k < steps; ++k) {
+    double t = static_cast<double>(k) * dt;
+    for (int j = 0; j < 3; ++j) {
+      const double h_j = w[j] * dt;
+      dts[static_cast<size_t>(3 * k + j)] = h_j;
+      ss[static_cast<size_t>(3 * k + j)] = T > 0.0 ? (t + 0.5 * h_j) / T : 0.5;
+      t += h_j;
+    }
+  }
+  return evolve_impl(h, psi, 0.0, 3 * steps, 0, 3 * steps, ss.data(), dts.data());
 }
 
 int qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_values, int64_t steps) {

@@ -79,6 +79,7 @@ struct GraphSpec {
   int* err = nullptr;  // bounded-wait error word of the TMA passes
   double dt = 0;
   const double* s_dev = nullptr;  // caller schedule on the device, or null for s_k = (k + 1/2)/K
+  const double* dt_dev = nullptr;  // per-step lengths on the device, or null for the uniform dt
   long long K = 0, k0 = 0, k1 = 0;
   int num_sms = 0;
   // graph scratch (graph_scratch_bytes): loop counter, kGraphUnroll + 1 P rows, kGraphUnroll B rows

@@ -81,7 +81,7 @@ cudaError_t build_evolve_graph(const GraphSpec& s, cudaGraphExec_t* out) {
   std::vector<Pass> passes;
   auto rows = [&](int dst_p0, long long p_first, int nprow, long long k_first, int nbrow, const long long* ctr) {
     return launch_graph_rows(lc, s.prow, dst_p0, p_first, nprow, s.brow, k_first, nbrow, ctr, plan.n, s.m, s.dt,
-                             s.s_dev, s.K, s.k0, s.k1, plan.wht_kind == kRotationForm);
+                             s.s_dev, s.K, s.k0, s.k1, plan.wht_kind == kRotationForm, s.dt_dev);
   };
   std::vector<cudaGraphNode_t> chain;
   auto add_child = [&](cudaGraph_t child) -> cudaError_t {

@@ -231,12 +231,21 @@ __device__ __forceinline__ double sched_s(const double* s_dev, long long K, long
   return s_dev ? s_dev[k] : (static_cast<double>(k) + 0.5) / static_cast<double>(K);
 }
 
-__device__ __noinline__ float2 p_entry(double dt, const double* s_dev, long long K, long long k0, long long k1,
-                                       long long p, int e) {
+// With dt_dev (sub-steps of individual length, e.g. the fourth-order triple
+// jump) the two half phases are weighted by their own lengths:
+//   theta_p = 1/2 ( dt_(k0+p-1) s_(k0+p-1) [p >= 1] + dt_(k0+p) s_(k0+p) [p < k1-k0] ).
+__device__ __noinline__ float2 p_entry(double dt, const double* dt_dev, const double* s_dev, long long K, long long k0,
+                                       long long k1, long long p, int e) {
   double th = 0.0;
-  if (p >= 1) th += sched_s(s_dev, K, k0 + p - 1);
-  if (p < k1 - k0) th += sched_s(s_dev, K, k0 + p);
-  th *= 0.5 * dt;
+  if (dt_dev) {
+    if (p >= 1) th += dt_dev[k0 + p - 1] * sched_s(s_dev, K, k0 + p - 1);
+    if (p < k1 - k0) th += dt_dev[k0 + p] * sched_s(s_dev, K, k0 + p);
+    th *= 0.5;
+  } else {
+    if (p >= 1) th += sched_s(s_dev, K, k0 + p - 1);
+    if (p < k1 - k0) th += sched_s(s_dev, K, k0 + p);
+    th *= 0.5 * dt;
+  }
   double sn, cs;
   sincos(th * static_cast<double>(e), &sn, &cs);
   return make_float2(static_cast<float>(cs), static_cast<float>(-sn));
@@ -245,9 +254,10 @@ __device__ __noinline__ float2 p_entry(double dt, const double* s_dev, long long
 // With rot set (rotation form) the row instead holds exp(-i dt (1 - s_k) q)
 // unscaled for q = 0..6, the rest zero: the per-block popcount phases of the
 // rotation form's 5- and 6-qubit Walsh-Hadamard sandwiches.
-__device__ __noinline__ float2 b_entry(double dt, const double* s_dev, long long K, long long k, int q, double scale,
-                                       int rot) {
+__device__ __noinline__ float2 b_entry(double dt, const double* dt_dev, const double* s_dev, long long K, long long k,
+                                       int q, double scale, int rot) {
   const double s = sched_s(s_dev, K, k);
+  if (dt_dev) dt = dt_dev[k];
   if (rot) {
     if (q > 6) return make_float2(0.f, 0.f);
     scale = 1.0;
@@ -261,8 +271,8 @@ __device__ __noinline__ float2 b_entry(double dt, const double* s_dev, long long
 // Phase tables for the steps c0 <= k < c1 of a range [k0, k1): P row rho is
 // position p = c0 - k0 + rho, B row rho is step k = c0 + rho.
 __global__ void tables_kernel(float2* __restrict__ ptab, float2* __restrict__ btab, int n, int m, double dt,
-                              const double* __restrict__ s_dev, long long K, long long k0, long long k1,
-                              long long c0, long long c1, double scale, int rot) {
+                              const double* __restrict__ dt_dev, const double* __restrict__ s_dev, long long K,
+                              long long k0, long long k1, long long c0, long long c1, double scale, int rot) {
   const long long prow_n = c1 - c0 + 1, brow_n = c1 - c0;
   const long long np = prow_n * (m + 1), nb = brow_n * (n + 1);
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np + nb;
@@ -270,12 +280,12 @@ __global__ void tables_kernel(float2* __restrict__ ptab, float2* __restrict__ bt
     if (i < np) {
       const long long rho = i / (m + 1);
       const int e = static_cast<int>(i - rho * (m + 1));
-      ptab[i] = p_entry(dt, s_dev, K, k0, k1, c0 - k0 + rho, e);
+      ptab[i] = p_entry(dt, dt_dev, s_dev, K, k0, k1, c0 - k0 + rho, e);
     } else {
       const long long j = i - np;
       const long long rho = j / (n + 1);
       const int q = static_cast<int>(j - rho * (n + 1));
-      btab[j] = b_entry(dt, s_dev, K, c0 + rho, q, scale, rot);
+      btab[j] = b_entry(dt, dt_dev, s_dev, K, c0 + rho, q, scale, rot);
     }
   }
 }
@@ -287,8 +297,8 @@ __global__ void tables_kernel(float2* __restrict__ ptab, float2* __restrict__ bt
 __global__ void graph_rows_kernel(float2* __restrict__ prow, int dst_p0, long long p_first, int nprow,
                                   float2* __restrict__ brow, long long k_first, int nbrow,
                                   const long long* __restrict__ ctr, int n, int m, double dt,
-                                  const double* __restrict__ s_dev, long long K, long long k0, long long k1,
-                                  double scale, int rot) {
+                                  const double* __restrict__ dt_dev, const double* __restrict__ s_dev, long long K,
+                                  long long k0, long long k1, double scale, int rot) {
   const long long off = ctr ? *ctr : 0;
   const long long np = static_cast<long long>(nprow) * (m + 1), nb = static_cast<long long>(nbrow) * (n + 1);
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np + nb;
@@ -296,12 +306,12 @@ __global__ void graph_rows_kernel(float2* __restrict__ prow, int dst_p0, long lo
     if (i < np) {
       const long long j = i / (m + 1);
       const int e = static_cast<int>(i - j * (m + 1));
-      prow[(dst_p0 + j) * (m + 1) + e] = p_entry(dt, s_dev, K, k0, k1, p_first + off + j, e);
+      prow[(dst_p0 + j) * (m + 1) + e] = p_entry(dt, dt_dev, s_dev, K, k0, k1, p_first + off + j, e);
     } else {
       const long long t = i - np;
       const long long j = t / (n + 1);
       const int q = static_cast<int>(t - j * (n + 1));
-      brow[t] = b_entry(dt, s_dev, K, k_first + off + j, q, scale, rot);
+      brow[t] = b_entry(dt, dt_dev, s_dev, K, k_first + off + j, q, scale, rot);
     }
   }
 }
@@ -391,13 +401,14 @@ cudaError_t launch_init_uniform(const LaunchCtx& lc, float2* psi, int n) {
 
 cudaError_t launch_graph_rows(const LaunchCtx& lc, float2* prow, int dst_p0, long long p_first, int nprow, float2* brow,
                               long long k_first, int nbrow, const long long* ctr, int n, int m, double dt,
-                              const double* s_dev, long long K, long long k0, long long k1, bool rot) {
+                              const double* s_dev, long long K, long long k0, long long k1, bool rot,
+                              const double* dt_dev) {
   const long long total = static_cast<long long>(nprow) * (m + 1) + static_cast<long long>(nbrow) * (n + 1);
   long long grid = (total + 127) / 128;
   if (grid > 2ll * lc.num_sms) grid = 2ll * lc.num_sms;
   if (grid < 1) grid = 1;
   graph_rows_kernel<<<static_cast<unsigned>(grid), 128, 0, lc.stream>>>(
-      prow, dst_p0, p_first, nprow, brow, k_first, nbrow, ctr, n, m, dt, s_dev, K, k0, k1,
+      prow, dst_p0, p_first, nprow, brow, k_first, nbrow, ctr, n, m, dt, dt_dev, s_dev, K, k0, k1,
       exp2(-static_cast<double>(n)), rot ? 1 : 0);
   return cudaGetLastError();
 }
@@ -410,13 +421,13 @@ cudaError_t launch_graph_advance(const LaunchCtx& lc, long long* ctr, long long 
 
 cudaError_t launch_tables(const LaunchCtx& lc, float2* ptab, float2* btab, int n, int m, double dt,
                           const double* s_dev, long long K, long long k0, long long k1, long long c0, long long c1,
-                          bool rot) {
+                          bool rot, const double* dt_dev) {
   const long long total = (c1 - c0 + 1) * (m + 1) + (c1 - c0) * (n + 1);
   long long grid = (total + 255) / 256;
   if (grid > 4ll * lc.num_sms) grid = 4ll * lc.num_sms;
   if (grid < 1) grid = 1;
-  tables_kernel<<<static_cast<unsigned>(grid), 256, 0, lc.stream>>>(ptab, btab, n, m, dt, s_dev, K, k0, k1, c0, c1,
-                                                                    exp2(-static_cast<double>(n)), rot ? 1 : 0);
+  tables_kernel<<<static_cast<unsigned>(grid), 256, 0, lc.stream>>>(ptab, btab, n, m, dt, dt_dev, s_dev, K, k0, k1,
+                                                                    c0, c1, exp2(-static_cast<double>(n)), rot ? 1 : 0);
   return cudaGetLastError();
 }
 

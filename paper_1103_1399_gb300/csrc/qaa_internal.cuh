@@ -76,9 +76,10 @@ cudaError_t launch_init_uniform(const LaunchCtx& lc, float2* psi, int n);
 // Phase tables for steps c0 <= k < c1 of the range [k0, k1) of a K-step run:
 // c1-c0+1 P rows of m+1 entries and c1-c0 B rows of n+1 entries.
 // rot: B rows in the rotation form's layout (entries q = 0..6 = exp(-i dt (1 - s_k) q), unscaled).
+// dt_dev: per-step lengths (device, K entries) instead of the uniform dt.
 cudaError_t launch_tables(const LaunchCtx& lc, float2* ptab, float2* btab, int n, int m, double dt,
                           const double* s_dev, long long K, long long k0, long long k1, long long c0, long long c1,
-                          bool rot = false);
+                          bool rot = false, const double* dt_dev = nullptr);
 cudaError_t launch_pass(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m,
                         const ClauseLP* cl, const float2* ptab, const float2* btab);
 // Launch-graph helpers: phase rows from the same entry functions as
@@ -87,7 +88,8 @@ cudaError_t launch_pass(const LaunchCtx& lc, const Pass& p, float2* psi, int n, 
 // that advances *ctr by `step` and sets the WHILE condition to *ctr < limit.
 cudaError_t launch_graph_rows(const LaunchCtx& lc, float2* prow, int dst_p0, long long p_first, int nprow, float2* brow,
                               long long k_first, int nbrow, const long long* ctr, int n, int m, double dt,
-                              const double* s_dev, long long K, long long k0, long long k1, bool rot = false);
+                              const double* s_dev, long long K, long long k0, long long k1, bool rot = false,
+                              const double* dt_dev = nullptr);
 cudaError_t launch_graph_advance(const LaunchCtx& lc, long long* ctr, long long step, long long limit,
                                  cudaGraphConditionalHandle h);
 // n <= kOnchipMaxBits: the whole state stays in one CTA's shared memory for
