@@ -312,6 +312,32 @@ def small_configs(q, torch, stream):
     return out
 
 
+def spectrum_lines(q, torch, n, clauses):
+    import satgen
+    out = {}
+    cl20 = satgen.load_instance("planted_n20_s0")["clauses"]
+    scan = []
+    t0 = time.perf_counter()
+    with q.Instance(20, cl20) as inst:
+        for s in [0.1 * i for i in range(1, 10)]:
+            lv, its = inst.lowest_eigenvalues(s, k=2, max_iter=200, start=0)
+            scan.append({"s": round(s, 2), "e0": lv[0], "gap": lv[1] - lv[0] if len(lv) > 1 else None, "iters": its})
+    wall = time.perf_counter() - t0
+    gaps = [r["gap"] for r in scan if r["gap"] is not None]
+    out["n20_gap_scan"] = {"points": scan, "min_gap": min(gaps) if gaps else None, "wall_s": wall,
+                           "what": "qaa_lowest_eigenvalues(s, k=2, 200 iterations, uniform start) at s = 0.1..0.9"}
+    torch.cuda.empty_cache()
+    with q.Instance(n, clauses) as inst:
+        inst.lowest_eigenvalues(0.5, k=1, max_iter=2, start=0)  # workspace allocation, E(x) export
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lv, its = inst.lowest_eigenvalues(0.5, k=2, max_iter=30, start=0)
+        wall = time.perf_counter() - t0
+    out[f"n{n}_lanczos"] = {"s": 0.5, "iters": its, "ms_per_iter": 1e3 * wall / its, "ritz_lowest": lv,
+                            "what": "30 Lanczos iterations at n=30 (H v by direct gathers, FP64 vectors), host-timed"}
+    return out
+
+
 def autotune_sizes(q, torch, work):
     """qaa_autotune once per streaming size of the mix (n >= 15), on the first
     request of that size; the chosen plans then serve every later handle and
@@ -525,6 +551,13 @@ def run_ours(args):
                   "what": "qaa_evolve_order4: each step of dt = 0.1 is three Strang sub-steps (Yoshida weights)"}
         oi.close()
 
+    # spectrum of H(s) by Lanczos: the gap scan of the 20-qubit instance over
+    # s = 0.1 .. 0.9 (levels reachable from the uniform state), and the cost of
+    # one Lanczos iteration at n = 30 (three FP64 vectors of 8 GiB)
+    spectrum = None
+    if not args.no_spectrum and rank == 0:
+        spectrum = spectrum_lines(q, torch, n, clauses)
+
     # the 32-qubit case of the same configuration (32 GiB state), a short run
     n32 = None
     if not args.no_n32 and rank == 0:
@@ -621,6 +654,7 @@ def run_ours(args):
             "e2e": e2e,
             "precision_variants": variants,
             "launch_graph": graph,
+            "spectrum": spectrum,
             "order4": order4,
             "small_configs": small,
             "n32": n32,
@@ -647,6 +681,7 @@ def main():
                     help="skip timing the tensor-core WHT variants and the launch-graph mode")
     ap.add_argument("--no-n32", action="store_true", help="skip the short 32-qubit (32 GiB) run")
     ap.add_argument("--no-small", action="store_true", help="skip the n=12 and n=20 configuration lines")
+    ap.add_argument("--no-spectrum", action="store_true", help="skip the Lanczos spectrum lines")
     ap.add_argument("--serving-requests", type=int, default=1024,
                     help="requests in the batched-serving measurement (0 skips it)")
     ap.add_argument("--instance", default=INSTANCE,

@@ -155,6 +155,31 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
  * descriptions one per line in buf (NULL allowed).  Needs no GPU. */
 int qaa_tune_candidates(int n, char* buf, size_t len);
 
+/*
+ * qaa_lowest_eigenvalues -- the k lowest levels of H(s) = (1 - s) H_B + s H_P
+ * (Eq. (1)) by Lanczos: the gap E1 - E0 bounds how slowly the evolution of
+ * Sec. 2.1 must sweep s to stay in the ground state.
+ *   start 0: from the uniform state, so only levels reachable from the initial
+ *            state of the evolution appear (the relevant gap); at s = 0 that is
+ *            the ground level alone.
+ *   start 1: from a real random vector (splitmix64 of the index and `seed`):
+ *            every level, each distinct level once.
+ *   max_iter Lanczos iterations (2..4000), fewer if the Krylov space is
+ *            exhausted; *iters (may be NULL) receives the count used.
+ *   evals    host array of k doubles: the lowest levels found, ascending;
+ *            *found = how many (<= k).
+ * FP64 real vectors (three arrays of 2^n doubles, allocated by the handle on
+ * first use; QAA_E_NOMEM if they do not fit), FP64 recurrence scalars and host
+ * tridiagonal eigenvalues (Sturm bisection); repeated and spurious Ritz values
+ * of finite-precision Lanczos are removed by the Cullum-Willoughby test
+ * (levels closer than 1e-9 ||T|| count as one).
+ * Synchronous.  QAA_E_ARG for k outside [1, 8], max_iter outside [2, 4000], a
+ * start other than 0 / 1 or a non-finite s.  The paper has no counterpart
+ * (it evolves without computing the spectrum).
+ */
+int qaa_lowest_eigenvalues(qaa_handle h, double s, int k, int max_iter, int start, uint64_t seed, double* evals,
+                           int* found, int* iters);
+
 /* Forget every plan recorded by qaa_autotune in this process. */
 int qaa_forget_tuned_plans(void);
 

@@ -34,7 +34,7 @@ is "parity unpinned".
 
 from .sat import violated_counts, energy_at, count_solutions, clause_is_violated
 from .hamiltonian import hb_dense, hp_dense, h_dense, sigma_x_dense
-from .spectrum import eigenvalues, sector_eigenvalues, sector_gap
+from .spectrum import eigenvalues, sector_eigenvalues, sector_gap, sparse_levels
 from .evolve import (
     midpoint_schedule,
     uniform_state,

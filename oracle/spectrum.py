@@ -42,3 +42,26 @@ def sector_gap(n, clauses, s):
     """E1 - E0 of the levels reachable from the uniform state (nan if fewer than two)."""
     lv = sector_eigenvalues(n, clauses, s, 2)
     return float(lv[1] - lv[0]) if len(lv) >= 2 else float("nan")
+
+
+def sparse_levels(n, clauses, s, k, level_tol=1e-8):
+    """The k lowest distinct levels of H(s) for larger n, from a sparse H
+    (H_B as the n bit-flip terms, H_P diagonal) and ARPACK (scipy eigsh) as the
+    eigensolver step; degenerate copies merge within level_tol."""
+    import scipy.sparse
+    import scipy.sparse.linalg
+    from .sat import violated_counts
+    dim = 1 << n
+    x = np.arange(dim, dtype=np.int64)
+    rows, cols, vals = [x], [x], [0.5 * n * (1.0 - s) + s * violated_counts(n, clauses).astype(np.float64)]
+    for i in range(n):
+        rows.append(x)
+        cols.append(x ^ (1 << i))
+        vals.append(np.full(dim, -0.5 * (1.0 - s)))
+    h = scipy.sparse.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(dim, dim))
+    lam = np.sort(scipy.sparse.linalg.eigsh(h, k=min(dim - 2, 4 * k + 8), which="SA", tol=1e-12)[0])
+    levels = []
+    for v in lam:
+        if not levels or v - levels[-1] > level_tol:
+            levels.append(float(v))
+    return np.array(levels[:k])

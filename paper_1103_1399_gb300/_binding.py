@@ -58,6 +58,8 @@ SIGNATURES = {
     "qaa_evolve_substeps": (_c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.c_int64]),
     "qaa_evolve_order4": (_c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int64]),
+    "qaa_lowest_eigenvalues": (_c_int, [_vp, ctypes.c_double, _c_int, _c_int, _c_int, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "qaa_autotune": (_c_int, [_vp, _vp, _c_int, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
     "qaa_tune_candidates": (_c_int, [_c_int, ctypes.c_char_p, ctypes.c_size_t]),
     "qaa_forget_tuned_plans": (_c_int, []),
@@ -243,6 +245,14 @@ class Instance:
         """The linear schedule in fourth-order (Yoshida triple-jump) steps (qaa_evolve_order4)."""
         _check_state(self, psi)
         _check(lib.qaa_evolve_order4(self._h, _ptr(psi), float(T), int(steps)))
+
+    def lowest_eigenvalues(self, s, k=2, max_iter=200, start=0, seed=0):
+        """Lowest k levels of H(s) by Lanczos (qaa_lowest_eigenvalues): (levels, iterations)."""
+        ev = (ctypes.c_double * k)()
+        found, its = _c_int(), _c_int()
+        _check(lib.qaa_lowest_eigenvalues(self._h, float(s), int(k), int(max_iter), int(start), int(seed), ev,
+                                          ctypes.byref(found), ctypes.byref(its)))
+        return [ev[i] for i in range(found.value)], its.value
 
     def observables(self, psi):
         _check_state(self, psi)

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqaa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["pass_kernels.cu", "obs_kernels.cu", "onchip.cu", "engine.cpp", "noalloc.cu", "tma_kernels.cu", "tc_kernels.cu", "plan.cpp", "serve.cpp", "persist.cu", "graph.cpp"]
+SOURCES = ["pass_kernels.cu", "obs_kernels.cu", "onchip.cu", "engine.cpp", "noalloc.cu", "tma_kernels.cu", "tc_kernels.cu", "plan.cpp", "serve.cpp", "persist.cu", "graph.cpp", "lanczos.cu"]
 
 
 def nvcc():

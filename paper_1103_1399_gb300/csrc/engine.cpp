@@ -71,6 +71,9 @@ struct qaa_ctx {
              k1 == o.k1 && wht_kind == o.wht_kind && stream == o.stream;
     }
   } gkey{};
+  // Lanczos workspace (qaa_lowest_eigenvalues), allocated on first use
+  void* d_lz = nullptr;
+  size_t lz_bytes = 0;
   // launch profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
@@ -381,6 +384,7 @@ int qaa_destroy(qaa_handle h) {
   cudaFree(h->d_lp);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   cudaFree(h->d_gscratch);
+  cudaFree(h->d_lz);
   cudaFree(h->d_tab);
   cudaFree(h->d_s);
   cudaFree(h->d_part);
@@ -593,6 +597,135 @@ int qaa_tune_candidates(int n, char* buf, size_t len) {
 int qaa_forget_tuned_plans(void) {
   qaa::clear_tuned_plans();
   return QAA_OK;
+}
+
+namespace {
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal a[0..m) and off-diagonal b[1..m) (Sturm sequence of the LDL^T
+// pivots).
+int sturm_count(const std::vector<double>& a, const std::vector<double>& b, int first, int m, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int i = first; i < m; ++i) {
+    const double off = i > first ? b[i] * b[i] : 0.0;
+    q = a[i] - x - (i > first ? off / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// All eigenvalues (ascending) of the tridiagonal matrix rows [first, m) by bisection.
+std::vector<double> tridiag_eigs(const std::vector<double>& a, const std::vector<double>& b, int first, int m) {
+  double lo = 0.0, hi = 0.0;
+  for (int i = first; i < m; ++i) {
+    const double r = (i > first ? std::fabs(b[i]) : 0.0) + (i + 1 < m ? std::fabs(b[i + 1]) : 0.0);
+    lo = i == first ? a[i] - r : std::min(lo, a[i] - r);
+    hi = i == first ? a[i] + r : std::max(hi, a[i] + r);
+  }
+  const double span = std::max(1.0, hi - lo);
+  std::vector<double> ev;
+  for (int k = 0; k < m - first; ++k) {
+    double l = lo - 1e-12 * span, r = hi + 1e-12 * span;
+    for (int it = 0; it < 200 && r - l > 1e-15 * span; ++it) {
+      const double mid = 0.5 * (l + r);
+      if (sturm_count(a, b, first, m, mid) > k) r = mid; else l = mid;
+    }
+    ev.push_back(0.5 * (l + r));
+  }
+  return ev;
+}
+
+}  // namespace
+
+int qaa_lowest_eigenvalues(qaa_handle h, double s, int k, int max_iter, int start, uint64_t seed, double* evals,
+                           int* found, int* iters) {
+  int st = check_handle(h);
+  if (st) return st;
+  if (!evals || !found) return fail(QAA_E_ARG, "evals or found is null");
+  if (k < 1 || k > 8) return fail(QAA_E_ARG, "k must be in [1, 8]");
+  if (max_iter < 2 || max_iter > 4000) return fail(QAA_E_ARG, "max_iter must be in [2, 4000]");
+  if (start != 0 && start != 1) return fail(QAA_E_ARG, "start must be 0 (uniform) or 1 (random)");
+  if (!std::isfinite(s)) return fail(QAA_E_ARG, "s must be finite");
+  const size_t N = size_t{1} << h->n;
+  const int P = qaa::lanczos_partials(h->num_sms);
+  const size_t vec = N * sizeof(double);
+  const size_t need = 3 * vec + ((N * sizeof(uint16_t) + 255) & ~size_t{255}) + sizeof(double) * (P + 2 * max_iter + 2);
+  if (need > h->lz_bytes) {
+    if (h->d_lz) {
+      QAA_CK(cudaStreamSynchronize(h->stream));
+      QAA_CK(cudaFree(h->d_lz));
+      h->d_lz = nullptr;
+      h->lz_bytes = 0;
+    }
+    if (cudaMalloc(&h->d_lz, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QAA_E_NOMEM, "cannot allocate the Lanczos workspace (3 state vectors)");
+    }
+    h->lz_bytes = need;
+  }
+  char* base = static_cast<char*>(h->d_lz);
+  qaa::LanczosArgs a;
+  a.n = h->n;
+  a.s = s;
+  a.iters = max_iter;
+  a.random_start = start;
+  a.seed = seed;
+  a.v = reinterpret_cast<double*>(base);
+  a.vp = reinterpret_cast<double*>(base + vec);
+  a.w = reinterpret_cast<double*>(base + 2 * vec);
+  uint16_t* E = reinterpret_cast<uint16_t*>(base + 3 * vec);
+  a.E = E;
+  double* dbl = reinterpret_cast<double*>(base + 3 * vec + ((N * sizeof(uint16_t) + 255) & ~size_t{255}));
+  a.partials = dbl;
+  a.alpha = dbl + P;
+  a.beta = dbl + P + max_iter;
+  const qaa::LaunchCtx lc = lctx(h);
+  QAA_CK(qaa::launch_hp_diag(lc, E, h->n, h->m, h->d_lp));
+  int done = 0;
+  QAA_CK(qaa::launch_lanczos(lc, a, &done));
+  std::vector<double> alpha(static_cast<size_t>(max_iter)), beta(static_cast<size_t>(max_iter) + 1);
+  QAA_CK(cudaMemcpyAsync(alpha.data(), a.alpha, sizeof(double) * max_iter, cudaMemcpyDeviceToHost, h->stream));
+  QAA_CK(cudaMemcpyAsync(beta.data(), a.beta, sizeof(double) * (max_iter + 1), cudaMemcpyDeviceToHost, h->stream));
+  QAA_CK(cudaStreamSynchronize(h->stream));
+  // Krylov space exhausted: stop at the first vanishing beta
+  double scale = 1.0;
+  for (int j = 0; j < max_iter; ++j) scale = std::max(scale, std::fabs(alpha[j]));
+  int m = max_iter;
+  for (int j = 0; j < max_iter; ++j)
+    if (!(beta[j + 1] > 1e-10 * scale)) {
+      m = j + 1;
+      break;
+    }
+  if (iters) *iters = m;
+  // Ritz values, then the Cullum-Willoughby test: in finite precision the
+  // Lanczos matrix T_m repeats converged eigenvalues and also has spurious
+  // ones; a simple eigenvalue of T_m that is also an eigenvalue of T_m without
+  // its first row and column is spurious, and repeated ones count once.
+  const std::vector<double> ev = tridiag_eigs(alpha, beta, 0, m);
+  const std::vector<double> evh = m > 1 ? tridiag_eigs(alpha, beta, 1, m) : std::vector<double>();
+  double tnorm = 1.0;
+  for (double x : ev) tnorm = std::max(tnorm, std::fabs(x));
+  const double tol = 1e-9 * tnorm;  // FP64 vectors: converged copies agree far below this
+  int nf = 0;
+  for (size_t i = 0; i < ev.size() && nf < k;) {
+    size_t j = i;
+    while (j + 1 < ev.size() && ev[j + 1] - ev[i] <= tol) ++j;
+    bool good = j > i;  // repeated: a converged eigenvalue
+    if (!good) {
+      good = true;
+      for (double y : evh)
+        if (std::fabs(y - ev[i]) <= tol) {
+          good = false;
+          break;
+        }
+    }
+    if (good || m == 1) evals[nf++] = ev[i];
+    i = j + 1;
+  }
+  *found = nf;
+  return check_device_error(h);
 }
 
 int qaa_set_launch_mode(qaa_handle h, int mode) {

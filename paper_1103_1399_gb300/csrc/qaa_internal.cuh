@@ -143,6 +143,25 @@ struct PersistPlan {
 cudaError_t launch_persist(const LaunchCtx& lc, const PersistPlan& pp, float2* psi, int n, int m, const ClauseLP* cl,
                            const float2* ptab, const float2* btab, int K, unsigned* bar, int* err, int grid);
 
+// Lanczos on H(s) (lanczos.cu): `iters` iterations from the uniform state or a
+// seeded random real vector; alpha[0..iters), beta[0..iters] (beta[0] = 0) in
+// device memory.  v, vp, w: 2^n real FP64 each; E: the exported H_P diagonal;
+// partials: lanczos_partials(num_sms) doubles.
+struct LanczosArgs {
+  int n = 0;
+  double s = 0;
+  int iters = 0;
+  int random_start = 0;
+  unsigned long long seed = 0;
+  const uint16_t* E = nullptr;
+  double *v = nullptr, *vp = nullptr, *w = nullptr;
+  double* partials = nullptr;
+  double* alpha = nullptr;
+  double* beta = nullptr;
+};
+int lanczos_partials(int num_sms);
+cudaError_t launch_lanczos(const LaunchCtx& lc, const LanczosArgs& a, int* done_iters);
+
 // Raise a kernel's dynamic shared-memory limit to `bytes` (its worst case over
 // every instance the library accepts) once per device.  Launches then request
 // only what they need; a per-launch limit would race between threads that

@@ -43,3 +43,10 @@ def test_planted_instance_gap_closes_in_the_middle():
     gaps = [oracle.sector_gap(8, cl, s) for s in np.linspace(0.05, 1.0, 20)]
     assert all(g > 0 for g in gaps)
     assert min(gaps) < gaps[0] and min(gaps) < gaps[-1]
+
+
+def test_sparse_levels_agree_with_dense():
+    cl = satgen.ratio_instance(9, 4, min_solutions=1)["clauses"]
+    for s in (0.2, 0.6):
+        dense = np.unique(np.round(oracle.eigenvalues(9, cl, s), 9))[:3]
+        assert np.allclose(oracle.sparse_levels(9, cl, s, 3), dense, atol=1e-8)
