@@ -271,6 +271,9 @@ cudaError_t launch_persist(const LaunchCtx& lc, const PersistPlan& pp, float2* p
     A.ga[g] = pp.ga[g];
     A.gq[g] = pp.gq[g];
   }
+  if (pp.ng < 1 || pp.ng > 3 || pp.phase_group < 0 || pp.phase_group >= pp.ng) return cudaErrorInvalidValue;
+  for (int g = 0; g < pp.ng; ++g)
+    if (pp.gq[g] < 5 || pp.gq[g] > 10) return cudaErrorInvalidValue;  // strided tiles of 5..10 bits only
   const size_t smem = persist_smem(m);
   cudaError_t e = allow_smem(reinterpret_cast<const void*>(persist_kernel), persist_smem(QAA_MAX_CLAUSES_DEV));
   if (e != cudaSuccess) return e;

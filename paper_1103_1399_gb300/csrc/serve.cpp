@@ -666,6 +666,7 @@ int qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, in
   // Persistent launches keep the phase tables of the whole run resident, so
   // they take runs of at most kPersistMaxSteps steps.
   r->persist = !r->plan.onchip && n <= s->persist_max_bits && steps <= kPersistMaxSteps;
+  if (r->persist) qaa::make_plan(n, r->plan, 10);  // the persistent kernel's tiles hold at most 10 bits
   r->graph = !r->plan.onchip && !r->persist && s->use_graphs;
   if (r->plan.onchip && qaa::onchip_smem_bytes(n, m) > 227u * 1024u) {
     delete r;
