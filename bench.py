@@ -43,9 +43,9 @@ FALLBACK_HBM_GBS = 6800.0
 TRAFFIC = {
     # ncu full-set capture of sp_tma_kernel<10,4,0> on the n=28 instance with
     # QAA_GROUP_BITS=10,8 (profiles/sp_tma_kernel_q10_run128_plain_n28.md):
-    # 2.147820e9 + 2.087194e9 bytes per launch for 2^28 amplitudes, scaled by the
+    # 2.149804e9 + 2.086487e9 bytes per launch for 2^28 amplitudes, scaled by the
     # amplitude count (x4) to one n=30 launch.
-    "strided": {"bytes_per_launch": 4 * (2.147820e9 + 2.087194e9), "src_sha": "dc613a84f599e051"},
+    "strided": {"bytes_per_launch": 4 * (2.149804e9 + 2.086487e9), "src_sha": "96e688e4fc26e95e"},
 }
 
 

@@ -202,6 +202,23 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
       for (int r = 0; r < 32; ++r) v[r] = src[(r << QB) << C];
     }
     if (MODE == 2) reg_rot<5>(v, *reinterpret_cast<const float2(*)[6]>(&rtab)); else reg_wht<0, 5>(v);  // i bits QB..QB+4
+    // A plain W pass is done with the buffer once layout L is read: the next
+    // tile's copy starts there, before the second butterfly stage, instead of
+    // after it (measured at n = 30: 3.08 -> 2.89 ms per pass).  The rotation
+    // form, also storing from layout L, ran slower with the early copy (3.67 ->
+    // 4.22 ms: its heavier second stage then overlaps the copies of all three
+    // CTAs on the SM) and keeps the late one.
+    constexpr bool kEarlyIssue = MODE == 0 && QB > 0;
+    auto issue_next = [&]() {
+      __syncthreads();
+      if (tid == 0) {
+        const long long Tn = T + stride_t;
+        if (Tn < ntiles) {
+          fence_proxy_async();
+          issue(static_cast<unsigned long long>(Tn));
+        }
+      }
+    };
     if (QB > 0) {
       __syncthreads();  // dense tile fully read
 #pragma unroll
@@ -209,6 +226,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = s_buf[sx_l + (r << C)];
+      if (kEarlyIssue) issue_next();
       stage_l<QB, C, MODE>(v, rtab, lane);  // i bits 0..QB-1
     }
     if (WBW) {
@@ -228,14 +246,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
       reg_wht<0, 5>(v);
     }
     // the buffer is free: fetch the next tile while this one is stored
-    __syncthreads();
-    if (tid == 0) {
-      const long long Tn = T + stride_t;
-      if (Tn < ntiles) {
-        fence_proxy_async();
-        issue(static_cast<unsigned long long>(Tn));
-      }
-    }
+    if (!kEarlyIssue) issue_next();
     if (WBW || QB == 0) {
       // layout H: i = th + (r << QB); th = i bits 0..QB-1: bits 0..4 lie at a1.., bit 5 (QB = 6) at a2
       float2* dst = psi + xbase + j + (static_cast<unsigned long long>(th & 31) << a1) +
