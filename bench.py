@@ -41,11 +41,12 @@ FALLBACK_HBM_GBS = 6800.0
 # for the dominant kernel, with the sha256 of the kernel sources at the time of
 # the capture; a mismatch (kernel changed since) reports traffic = null.
 TRAFFIC = {
-    # ncu full-set capture of sp_tma_kernel<10,4,0> on the n=28 instance with
-    # QAA_GROUP_BITS=10,8 (profiles/sp_tma_kernel_q10_run128_plain_n28.md):
-    # 2.149804e9 + 2.086487e9 bytes per launch for 2^28 amplitudes, scaled by the
-    # amplitude count (x4) to one n=30 launch.
-    "strided": {"bytes_per_launch": 4 * (2.149804e9 + 2.086487e9), "src_sha": "96e688e4fc26e95e"},
+    # ncu full-set capture of sp_tma_kernel<10,4,2> (the default rotation form's
+    # strided pass, 128-byte runs) on the n=28 instance with QAA_GROUP_BITS=10,8
+    # (profiles/sp_tma_kernel_q10_run128_rotation_n28.md): 2.147941e9 + 2.087141e9
+    # bytes per launch for 2^28 amplitudes, scaled by the amplitude count (x4) to
+    # one n=30 launch.
+    "strided": {"bytes_per_launch": 4 * (2.147941e9 + 2.087141e9), "src_sha": "7545b58b2fdb9397"},
 }
 
 
@@ -248,6 +249,13 @@ def _pct(v, p):
     return float(np.percentile(np.asarray(v), p)) if v else None
 
 
+def round_trips(plan_description):
+    """HBM round trips per Strang step of a streaming plan, from its description:
+    g strided groups -> g + 1 in the rotation form, 2g in the W.B.W form."""
+    g = plan_description.count("group bits")
+    return g + 1 if "rotation form" in plan_description else 2 * g
+
+
 def small_configs(q, torch, stream):
     """n = 12: ten planted instances (seeds 0..9), T = 20, 400 steps, solved one at
     a time through the handle API (the on-chip evolver): solves/s, P_succ, norm.
@@ -278,7 +286,7 @@ def small_configs(q, torch, stream):
     with q.Instance(20, cl20, stream=stream) as inst:
         inst.init_uniform(p20)
         inst.evolve(p20, 1.0, 20)  # warm-up
-        rts = 2 * inst.describe_plan().count("group bits")
+        rts = round_trips(inst.describe_plan())
         for T in (10.0, 40.0, 160.0):
             K = int(round(T / 0.05))
             inst.init_uniform(p20)
@@ -490,7 +498,9 @@ def run_ours(args):
     # tensor-core split-BF16 Walsh-Hadamard variants on the same workload
     variants = {}
     if not args.no_variants:
-        for kind, name in ((1, "bf16x3"), (2, "bf16x2"), (3, "rotation")):
+        default_form = 3 if "rotation form" in inst.describe_plan() else 0
+        forms = ((0, "wbw"), (1, "bf16x3"), (2, "bf16x2"), (3, "rotation"))
+        for kind, name in (f for f in forms if f[0] != default_form):
             vi = q.Instance(n, clauses, stream=stream)
             vi.set_variant(kind)
             vi.init_uniform(psi)
@@ -507,7 +517,7 @@ def run_ours(args):
             vms = e0.elapsed_time(e1)
             vprof = {k: {"launches": v[0], "ms": v[1]} for k, v in vi.profile_read().items() if v[0] > 0}
             vi.profile(False)
-            rts = passes_per_step if kind != 3 else vi.describe_plan().count("group bits") + 1
+            rts = round_trips(vi.describe_plan())
             variants[name] = {"steps_per_s": vk / (vms / 1e3), "ms_per_step": vms / vk, "steps": vk,
                               "hbm_round_trips_per_step": rts, "plan": vi.describe_plan(), "kernels": vprof,
                               "hbm_gbs": rts * 2 * state_bytes * vk / (vms / 1e3) / 1e9}
@@ -576,11 +586,12 @@ def run_ours(args):
         h1.record(stream)
         torch.cuda.synchronize()
         hms = h0.elapsed_time(h1)
-        rts = 2 * (i32.describe_plan().count("group bits"))
+        rts = round_trips(i32.describe_plan())
         n32 = {"steps_per_s": k32 / (hms / 1e3), "ms_per_step": hms / k32, "steps": k32, "plan": i32.describe_plan(),
                "hbm_gbs": rts * 2 * 8 * (1 << 32) * k32 / (hms / 1e3) / 1e9, "m": len(d32["clauses"])}
         if not args.no_variants:
-            i32.set_variant(3)
+            other = 0 if "rotation form" in i32.describe_plan() else 3
+            i32.set_variant(other)
             i32.init_uniform(p32)
             i32.evolve(p32, DT * 3, 3)
             torch.cuda.synchronize()
@@ -589,9 +600,10 @@ def run_ours(args):
             h1.record(stream)
             torch.cuda.synchronize()
             rms = h0.elapsed_time(h1)
-            rrt = i32.describe_plan().count("group bits") + 1
-            n32["rotation"] = {"steps_per_s": k32 / (rms / 1e3), "ms_per_step": rms / k32, "plan": i32.describe_plan(),
-                               "hbm_gbs": rrt * 2 * 8 * (1 << 32) * k32 / (rms / 1e3) / 1e9}
+            rrt = round_trips(i32.describe_plan())
+            n32["rotation" if other == 3 else "wbw"] = {
+                "steps_per_s": k32 / (rms / 1e3), "ms_per_step": rms / k32, "plan": i32.describe_plan(),
+                "hbm_gbs": rrt * 2 * 8 * (1 << 32) * k32 / (rms / 1e3) / 1e9}
         i32.close()
         del p32
         torch.cuda.empty_cache()

@@ -414,14 +414,10 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (wht_kind == qaa::kRotationForm && h->n > qaa::kOnchipMaxBits && !h->plan.use_tma)
     return fail(QAA_E_ARG, "the rotation form needs the TMA passes (not available, or QAA_PASSES=classic)");
   qaa::make_plan(h->n, h->plan, (wht_kind == 1 || wht_kind == 2) ? 10 : 11);  // no 11-bit tensor-core tiles
-  const bool tuned_rotation = h->plan.wht_kind == qaa::kRotationForm;  // keep a tuned plan's run lengths
+  // a plan made (or tuned) for the other form gets the run lengths of this one
+  const bool same_form = (h->plan.wht_kind == qaa::kRotationForm) == (wht_kind == qaa::kRotationForm);
   h->plan.wht_kind = wht_kind;
-  // The rotation form's passes carry more arithmetic than a plain W pass, which
-  // three 64 KiB-tile CTAs per SM hide better than one 128 KiB-tile CTA:
-  // measured at n = 30, 64-byte runs for both groups 10.91 ms per step, the
-  // W.B.W form's choice (128 / 64) 11.22 ms, 128-byte runs for both 11.78 ms.
-  if (wht_kind == qaa::kRotationForm && !tuned_rotation && !std::getenv("QAA_RUN128_GROUPS"))
-    for (int& c : h->plan.run_c) c = 0;
+  if (!same_form) qaa::set_default_run_c(h->plan);
   return QAA_OK;
 }
 
@@ -546,6 +542,7 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
   if (best.use_tma && narrow && spent() <= budget_ms) {
     qaa::PassPlan c = best;
     c.use_tma = false;
+    c.wht_kind = 0;  // plain loads: the W.B.W form only
     if (c.strided.size() == 2 && c.strided[0].a2 != c.strided[0].a + 5) {
       const int q = c.strided[0].q;
       c.strided[0] = {qaa::kLowBits, q, qaa::kLowBits + 5};

@@ -42,6 +42,8 @@ void make_plan(int n, PassPlan& plan, int max_q = 11);
 // QAA_PHASE_GROUP, QAA_RUN128_GROUPS and QAA_GROUP_BITS read from the
 // environment.
 void make_default_plan(int n, PassPlan& plan, int max_q = 11);
+// Run lengths per group for the plan's form (QAA_RUN128_GROUPS overrides).
+void set_default_run_c(PassPlan& plan);
 
 // Autotuner support.  First-round candidates for n >= 15: the default plan,
 // then every split of bits 10..n-1 into the fewest groups of 5..11 bits (5..10

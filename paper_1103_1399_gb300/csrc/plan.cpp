@@ -130,9 +130,8 @@ void plan_with_groups(int n, const std::vector<int>& sizes, int phase_group, boo
     a += q;
   }
   plan.phase_group = phase_group;
-  const int ng = static_cast<int>(sizes.size());
-  plan.run_c.assign(static_cast<size_t>(ng), 0);
-  for (int i = 0; i < ng; ++i) plan.run_c[i] = i == phase_group ? 0 : 4;
+  plan.wht_kind = 0;  // round 1 varies the W.B.W form's groups; round 5 tries the rotation form
+  set_default_run_c(plan);
 }
 
 void plan_candidates(int n, std::vector<PassPlan>& out) {
@@ -222,13 +221,31 @@ void make_default_plan(int n, PassPlan& plan, int max_q) {
     const int v = std::atoi(pg);
     if (v >= 0 && v < ng) plan.phase_group = v;
   }
-  // Contiguous run per tile row: 128 bytes for the plain strided passes, 64
-  // bytes (three CTAs per SM) for the heavier pass that hosts the phase.
+  // The form of the H_B factor: on the TMA FP32 passes the rotation form
+  // (W.diag.W on every 5-qubit block inside each pass: g round trips per
+  // step), otherwise the W.B.W form (2g - 2).
+  plan.wht_kind = plan.use_tma ? kRotationForm : 0;
+  set_default_run_c(plan);
+}
+
+void set_default_run_c(PassPlan& plan) {
+  // Contiguous run per tile row.  W.B.W form: 128 bytes for the plain strided
+  // passes, 64 bytes (three CTAs per SM) for the heavier pass that hosts the
+  // phase.  Rotation form: 128 bytes for every group (measured at n = 30: 8.97
+  // ms per step, against 9.74 with 64 bytes for one group and 10.56 for both;
+  // its passes start the next tile's copy before their second stage).
+  const int ng = static_cast<int>(plan.strided.size());
   const char* rg = std::getenv("QAA_RUN128_GROUPS");
   const int rmask = rg ? std::atoi(rg) : -1;
   plan.run_c.resize(static_cast<size_t>(ng));
-  for (int i = 0; i < ng; ++i)
-    plan.run_c[i] = rmask >= 0 ? (((rmask >> i) & 1) ? 4 : 0) : (i == plan.phase_group ? 0 : 4);
+  for (int i = 0; i < ng; ++i) {
+    if (rmask >= 0)
+      plan.run_c[i] = ((rmask >> i) & 1) ? 4 : 0;
+    else if (plan.wht_kind == kRotationForm)
+      plan.run_c[i] = 4;
+    else
+      plan.run_c[i] = i == plan.phase_group ? 0 : 4;
+  }
 }
 
 // Rotation form (variant 3): exp(-i theta H_B) = prod_i exp(-i theta (1 - sigma^x_i)/2),
@@ -291,7 +308,7 @@ std::string describe_plan(const PassPlan& plan) {
   if (plan.onchip) return "on-chip: whole run in one CTA's shared memory (n=" + std::to_string(plan.n) + ")";
   const int ng = static_cast<int>(plan.strided.size());
   if (plan.wht_kind == kRotationForm) {
-    std::string d = "streaming, TMA loads, rotation form (H_B as one-qubit rotations); low pass bits [0,10) R.P";
+    std::string d = "streaming, TMA loads, rotation form (H_B per 5-qubit block: W.diag.W); low pass bits [0,10) R.P";
     for (int i = 0; i < ng; ++i) {
       const Group& g = plan.strided[i];
       d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";

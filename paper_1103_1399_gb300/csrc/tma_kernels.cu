@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
     // form, also storing from layout L, ran slower with the early copy (3.67 ->
     // 4.22 ms: its heavier second stage then overlaps the copies of all three
     // CTAs on the SM) and keeps the late one.
-    constexpr bool kEarlyIssue = MODE == 0 && QB > 0;
+    constexpr bool kEarlyIssue = (MODE == 0 || (MODE == 2 && C >= 4)) && QB > 0;
     auto issue_next = [&]() {
       __syncthreads();
       if (tid == 0) {

@@ -200,6 +200,9 @@ def test_plan_description(env):
     q, _ = env
     with q.Instance(N, [[1, 2, 3]]) as inst:
         d = inst.describe_plan()
-    assert d.startswith("streaming") and "4 HBM round trips per step" in d
+    assert d.startswith("streaming") and "rotation form" in d and "3 HBM round trips per step" in d
+    with q.Instance(N, [[1, 2, 3]]) as inst:
+        inst.set_variant(0)
+        assert "W.B.W" in inst.describe_plan() and "4 HBM round trips per step" in inst.describe_plan()
     with q.Instance(12, [[1, 2, 3]]) as inst:
         assert inst.describe_plan().startswith("on-chip")
