@@ -43,10 +43,10 @@ FALLBACK_HBM_GBS = 6800.0
 TRAFFIC = {
     # ncu full-set capture of sp_tma_kernel<10,4,2> (the default rotation form's
     # strided pass, 128-byte runs) on the n=28 instance with QAA_GROUP_BITS=10,8
-    # (profiles/sp_tma_kernel_q10_run128_rotation_n28.md): 2.147941e9 + 2.087141e9
+    # (profiles/sp_tma_kernel_q10_run128_rotation_n28.md): 2.147558e9 + 2.087137e9
     # bytes per launch for 2^28 amplitudes, scaled by the amplitude count (x4) to
     # one n=30 launch.
-    "strided": {"bytes_per_launch": 4 * (2.147941e9 + 2.087141e9), "src_sha": "7545b58b2fdb9397"},
+    "strided": {"bytes_per_launch": 4 * (2.147558e9 + 2.087137e9), "src_sha": "56a58091bcd0fb80"},
 }
 
 

@@ -202,13 +202,13 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
       for (int r = 0; r < 32; ++r) v[r] = src[(r << QB) << C];
     }
     if (MODE == 2) reg_rot<5>(v, *reinterpret_cast<const float2(*)[6]>(&rtab)); else reg_wht<0, 5>(v);  // i bits QB..QB+4
-    // A plain W pass is done with the buffer once layout L is read: the next
-    // tile's copy starts there, before the second butterfly stage, instead of
-    // after it (measured at n = 30: 3.08 -> 2.89 ms per pass).  The rotation
-    // form, also storing from layout L, ran slower with the early copy (3.67 ->
-    // 4.22 ms: its heavier second stage then overlaps the copies of all three
-    // CTAs on the SM) and keeps the late one.
-    constexpr bool kEarlyIssue = (MODE == 0 || (MODE == 2 && C >= 4)) && QB > 0;
+    // Passes that store from layout L (plain W and the rotation form) are done
+    // with the buffer once layout L is read: the next tile's copy starts there,
+    // before the second butterfly stage, instead of after it (measured at
+    // n = 30: plain 3.08 -> 2.83 ms, rotation with 128-byte runs 2.70 ms).  A
+    // rotation pass with three 256-thread CTAs per SM ran slower with the early
+    // copy (3.67 -> 4.22 ms) and keeps the late one.
+    constexpr bool kEarlyIssue = (MODE == 0 || (MODE == 2 && G::NT >= 512)) && QB > 0;
     auto issue_next = [&]() {
       __syncthreads();
       if (tid == 0) {
