@@ -126,17 +126,17 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q);
  */
 /*
  * qaa_autotune -- choose the pass plan of a streaming-size handle (n >= 15)
- * by timing candidates on the GPU.  Round 1 times the default plan and every
+ * by timing candidates on the GPU.  Stage 1 times the default plan and every
  * split of bits 10..n-1 into the fewest strided groups of 5..10 bits (qubits
  * per pass) with every choice of the group that hosts the popcount phase;
- * round 2 toggles the contiguous run per tile row (64 or 128 bytes) of each
- * group of >= 7 bits; round 3 tries recombining two 10-bit groups; round 4
- * plain loads instead of TMA; round 5 the rotation form of the H_B factor
+ * stage 2 toggles the contiguous run per tile row (64 or 128 bytes) of each
+ * group of >= 7 bits; stage 3 tries recombining two 10-bit groups; stage 4
+ * plain loads instead of TMA; stage 5 the rotation form of the H_B factor
  * (variant 3, see qaa_set_variant) on the best plan so far, and if it wins,
- * the run-length toggles of round 2 again.  A handle on a
- * tensor-core variant (1, 2) keeps it and skips round 5.  Each candidate is timed with CUDA events as the
+ * the run-length toggles of stage 2 again.  A handle on a
+ * tensor-core variant (1, 2) keeps it and skips stage 5.  Each candidate is timed with CUDA events as the
  * best of two runs of `steps` Strang steps (1..64) after one untimed run.
- * Rounds stop once budget_ms of host time is spent (<= 0: 60 s); round 1's
+ * Stages stop once budget_ms of host time is spent (<= 0: 60 s); stage 1's
  * first candidate always runs.
  *   psi      device complex64[2^n], 16-byte aligned: scratch, overwritten
  *            (re-initialise it afterwards).
@@ -151,7 +151,7 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q);
  */
 int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* report, size_t len);
 
-/* Number of round-1 autotune candidates for n (0 for n <= 14), with their
+/* Number of stage-1 autotune candidates for n (0 for n <= 14), with their
  * descriptions one per line in buf (NULL allowed).  Needs no GPU. */
 int qaa_tune_candidates(int n, char* buf, size_t len);
 

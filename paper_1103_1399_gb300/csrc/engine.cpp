@@ -500,7 +500,7 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
       best = cand;
     }
   };
-  // round 1: group widths and the phase group
+  // stage 1: group widths and the phase group
   std::vector<qaa::PassPlan> cands;
   qaa::plan_candidates(h->n, cands);
   for (const auto& c : cands) {
@@ -513,7 +513,7 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
     qaa::make_plan(h->n, h->plan);
     return finish(fail(QAA_E_CUDA, "autotune: no candidate plan ran"));
   }
-  // round 2: run length of each group that has a choice (Q >= 7 on TMA passes)
+  // stage 2: run length of each group that has a choice (Q >= 7 on TMA passes)
   if (best.use_tma)
     for (size_t i = 0; i < best.strided.size() && spent() <= budget_ms; ++i) {
       if (best.strided[i].q < 7) continue;
@@ -521,7 +521,7 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
       c.run_c[i] = c.run_c[i] == 4 ? 0 : 4;
       consider(c);
     }
-  // round 3: two equal q-bit groups (q >= 10) recombined as {10..14, 15+q..} and {15..14+q}, or back
+  // stage 3: two equal q-bit groups (q >= 10) recombined as {10..14, 15+q..} and {15..14+q}, or back
   if (best.use_tma && best.strided.size() == 2 && best.strided[0].q == best.strided[1].q && best.strided[0].q >= 10 &&
       spent() <= budget_ms) {
     qaa::PassPlan c = best;
@@ -536,7 +536,7 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
     }
     consider(c);
   }
-  // round 4: plain loads instead of TMA (groups of at most 10 bits, contiguous)
+  // stage 4: plain loads instead of TMA (groups of at most 10 bits, contiguous)
   bool narrow = true;
   for (const auto& g : best.strided) narrow = narrow && g.q <= 10;
   if (best.use_tma && narrow && spent() <= budget_ms) {
@@ -550,7 +550,7 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
     }
     consider(c);
   }
-  // round 5: the rotation form of the H_B factor on the best plan (same step,
+  // stage 5: the rotation form of the H_B factor on the best plan (same step,
   // g instead of 2g - 2 round trips; FP32 CUDA-core passes only)
   if (!tc_kind && best.use_tma && spent() <= budget_ms) {
     qaa::PassPlan c = best;

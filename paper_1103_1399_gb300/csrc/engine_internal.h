@@ -45,7 +45,7 @@ void make_default_plan(int n, PassPlan& plan, int max_q = 11);
 // Run lengths per group for the plan's form (QAA_RUN128_GROUPS overrides).
 void set_default_run_c(PassPlan& plan);
 
-// Autotuner support.  First-round candidates for n >= 15: the default plan,
+// Autotuner support.  First-stage candidates for n >= 15: the default plan,
 // then every split of bits 10..n-1 into the fewest groups of 5..11 bits (5..10
 // without TMA; the fewest HBM round trips) with every choice of phase group;
 // run lengths 128 B for plain groups and 64 B for the phase group.

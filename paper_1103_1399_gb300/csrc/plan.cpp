@@ -130,7 +130,7 @@ void plan_with_groups(int n, const std::vector<int>& sizes, int phase_group, boo
     a += q;
   }
   plan.phase_group = phase_group;
-  plan.wht_kind = 0;  // round 1 varies the W.B.W form's groups; round 5 tries the rotation form
+  plan.wht_kind = 0;  // stage 1 varies the W.B.W form's groups; stage 5 tries the rotation form
   set_default_run_c(plan);
 }
 

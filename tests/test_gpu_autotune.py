@@ -42,7 +42,7 @@ def test_autotune_picks_a_timed_plan_and_records_it(env, n):
             assert inst.describe_plan() == plan
             timed = [ln.split("ms/step", 1)[1].strip() for ln in rep.splitlines() if "ms/step" in ln and not ln.startswith("chosen")]
             assert plan in timed
-            assert len(timed) >= len(q.tune_candidates(n))  # round 1 ran in full within the budget
+            assert len(timed) >= len(q.tune_candidates(n))  # stage 1 ran in full within the budget
             # the tuned plan still matches the oracle
             K, T = 12, 1.2
             inst.init_uniform(psi)
