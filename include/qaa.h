@@ -194,6 +194,11 @@ int qaa_init_uniform(qaa_handle h, void* psi);
  * qaa_evolve -- evolve psi in place from s = 0 to s = 1 over total time T with
  * `steps` Strang steps (dt = T/steps), Eq. (1) with the linear sweep s = t/T.
  * T >= 0, steps >= 1.  Asynchronous on the handle's stream.
+ * For n >= 15 on the TMA passes the handle stores, on the first evolution,
+ * the bit-sliced violated-clause counts of every 1024-amplitude tile (1.375
+ * bytes per amplitude: 1.4 GiB at n = 30) so that later low passes read them
+ * instead of counting again; if that memory cannot be allocated the passes
+ * count on the fly (the same values).  QAA_LP_COUNTS=0 turns the store off.
  */
 int qaa_evolve(qaa_handle h, void* psi, double T, int64_t steps);
 

@@ -71,6 +71,11 @@ struct qaa_ctx {
              k1 == o.k1 && wht_kind == o.wht_kind && stream == o.stream;
     }
   } gkey{};
+  // stored per-tile clause counts for the merged low passes: 0 = not yet
+  // computed, 1 = valid, -1 = not used (no TMA passes, no memory, or
+  // QAA_LP_COUNTS=0)
+  unsigned* d_counts = nullptr;
+  int counts_state = 0;
   // Lanczos workspace (qaa_lowest_eigenvalues), allocated on first use
   void* d_lz = nullptr;
   size_t lz_bytes = 0;
@@ -183,6 +188,28 @@ int prof_kind(int pass_kind) {
   }
 }
 
+// The stored per-tile clause counts, computed on the handle's stream the first
+// time a streaming evolution needs them; null when they are not used.
+const unsigned* stored_counts(qaa_ctx* h) {
+  if (h->counts_state == 0) {
+    const char* env = std::getenv("QAA_LP_COUNTS");
+    const bool want = h->plan.use_tma && h->n > qaa::kOnchipMaxBits && !(env && std::atoi(env) == 0);
+    h->counts_state = -1;
+    if (want && cudaMalloc(&h->d_counts, qaa::lp_counts_bytes(h->n)) == cudaSuccess) {
+      if (qaa::launch_lp_counts(lctx(h), h->d_counts, h->n, h->m, h->d_lp) == cudaSuccess) {
+        h->counts_state = 1;
+      } else {
+        cudaGetLastError();
+        cudaFree(h->d_counts);
+        h->d_counts = nullptr;
+      }
+    } else {
+      cudaGetLastError();
+    }
+  }
+  return h->counts_state == 1 ? h->d_counts : nullptr;
+}
+
 // Streaming plan, launch-graph mode: build (or reuse) the graph of the whole
 // range and launch it.  The graph is rebuilt when psi, the schedule, the range,
 // the variant or the stream changes.
@@ -210,6 +237,7 @@ int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, 
     gs.dt = dt;
     gs.s_dev = s_dev;
     gs.dt_dev = dt_dev;
+    gs.counts = stored_counts(h);
     gs.K = K;
     gs.k0 = k0;
     gs.k1 = k1;
@@ -282,9 +310,10 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
       }));
     } else {
       qaa::build_passes(h->plan, k0, k1, c0, c1, passes);
+      const unsigned* counts = stored_counts(h);
       for (const qaa::Pass& ps : passes)
         QAA_CK(timed(h, prof_kind(ps.kind), [&] {
-          return qaa::launch_planned_pass(lc, h->plan, ps, p, h->m, h->d_lp, ptab, btab, h->d_err);
+          return qaa::launch_planned_pass(lc, h->plan, ps, p, h->m, h->d_lp, ptab, btab, h->d_err, counts);
         }));
     }
   }
@@ -385,6 +414,7 @@ int qaa_destroy(qaa_handle h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   cudaFree(h->d_gscratch);
   cudaFree(h->d_lz);
+  cudaFree(h->d_counts);
   cudaFree(h->d_tab);
   cudaFree(h->d_s);
   cudaFree(h->d_part);

@@ -45,7 +45,7 @@ cudaError_t capture_into(cudaStream_t st, cudaGraph_t into, F&& body) {
 
 cudaError_t launch_all(const LaunchCtx& lc, const GraphSpec& s, const std::vector<Pass>& passes) {
   for (const Pass& p : passes) {
-    const cudaError_t e = launch_planned_pass(lc, *s.plan, p, s.psi, s.m, s.cl, s.prow, s.brow, s.err);
+    const cudaError_t e = launch_planned_pass(lc, *s.plan, p, s.psi, s.m, s.cl, s.prow, s.brow, s.err, s.counts);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -345,10 +345,10 @@ cudaError_t allow_smem(const void* func, size_t bytes) {
 }
 
 cudaError_t launch_planned_pass(const LaunchCtx& lc, const PassPlan& plan, const Pass& p, float2* psi, int m,
-                                const ClauseLP* cl, const float2* ptab, const float2* btab, int* err) {
-  if (plan.wht_kind == kRotationForm) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err);
+                                const ClauseLP* cl, const float2* ptab, const float2* btab, int* err, const unsigned* counts) {
+  if (plan.wht_kind == kRotationForm) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err, counts);
   if (plan.wht_kind) return launch_pass_tc(lc, p, psi, plan.n, m, cl, ptab, btab, plan.wht_kind == 1 ? 3 : 2);
-  if (plan.use_tma) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err);
+  if (plan.use_tma) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err, counts);
   return launch_pass(lc, p, psi, plan.n, m, cl, ptab, btab);
 }
 

@@ -122,8 +122,14 @@ cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, in
 // device word set to nonzero when a bounded wait expires.  psi must be 16-byte
 // aligned.
 bool tma_available();
+// counts (optional): the stored per-tile violated-clause counts of
+// launch_lp_counts, read by the merged low passes instead of counting again.
 cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
-                            const float2* ptab, const float2* btab, int* err);
+                            const float2* ptab, const float2* btab, int* err, const unsigned* counts = nullptr);
+// Per-tile bit-sliced violated-clause counts of every 1024-amplitude tile
+// (lp_counts_bytes(n) bytes), computed once per instance.
+size_t lp_counts_bytes(int n);
+cudaError_t launch_lp_counts(const LaunchCtx& lc, unsigned* counts, int n, int m, const ClauseLP* cl);
 
 // Tensor-core variant (tc_kernels.cu): the Walsh-Hadamard transforms of every
 // streaming pass as 16 x 16 Hadamard blocks on BF16-split operands (parts = 3:

@@ -316,10 +316,26 @@ __device__ __forceinline__ void xpose_y2x_t(float2 (&v)[32], float2* __restrict_
 
 // KIND kLpPhase / kLpRot: the rotation form (P alone; the rotations of bits
 // 0..9 then 2^-n P), with B row entries 0..5 = exp(-i theta p).
+// Stored per-tile counts (layout Y: registers hold bits 0..4): for tile t and
+// lane l, word (t * kCountWords + b) * 32 + l holds bit plane b of the lane's 32
+// violated-clause counts (b < kPlanes), and word kPlanes the tile's constant
+// part.  E(x) never changes during a run, so the merged low passes can read
+// these instead of folding and counting the clauses again every step.
+constexpr int kCountWords = kPlanes + 1;
+
+__device__ __forceinline__ void load_counts(const unsigned* __restrict__ counts, long long tile, int lane,
+                                            unsigned (&pl)[kPlanes], int& nconst) {
+  const unsigned* c = counts + static_cast<size_t>(tile) * (kCountWords * 32) + lane;
+#pragma unroll
+  for (int b = 0; b < kPlanes; ++b) pl[b] = __ldg(c + 32 * b);
+  nconst = static_cast<int>(__ldg(c + 32 * kPlanes));
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     lp_tma_kernel(float2* __restrict__ psi, int m, const ClauseLP* __restrict__ cl, const float2* __restrict__ prow,
-                  const float2* __restrict__ brow, int n, long long ntiles, int* __restrict__ err) {
+                  const float2* __restrict__ brow, int n, long long ntiles, int* __restrict__ err,
+                  const unsigned* __restrict__ counts) {
   constexpr bool kRegLow = KIND != kLpFirst && KIND != kLpPhase;  // phase applied in layout Y
   extern __shared__ __align__(1024) unsigned char smem[];
   const LpTmaLayout L(m);
@@ -353,9 +369,14 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
 
   int nconst = 0, npad = 0;
   unsigned pl[kPlanes];
+  const bool stored = kRegLow && counts != nullptr;
   if (first < ntiles) {
-    fold_tile<kRegLow>(s_cl, m, static_cast<unsigned>(first), lane, s_act, nconst, npad);
-    count_active(s_act, npad, 1u << lane, pl);
+    if (stored) {
+      load_counts(counts, first, lane, pl, nconst);
+    } else {
+      fold_tile<kRegLow>(s_cl, m, static_cast<unsigned>(first), lane, s_act, nconst, npad);
+      count_active(s_act, npad, 1u << lane, pl);
+    }
   }
   int it = 0;
   for (long long tile = first; tile < ntiles; tile += step, ++it) {
@@ -404,9 +425,13 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
 #pragma unroll
     for (int r = 0; r < 32; ++r) g[32 * r] = v[r];
     if (tn < ntiles) {
-      __syncwarp();
-      fold_tile<kRegLow>(s_cl, m, static_cast<unsigned>(tn), lane, s_act, nconst, npad);
-      count_active(s_act, npad, 1u << lane, pl);
+      if (stored) {
+        load_counts(counts, tn, lane, pl, nconst);
+      } else {
+        __syncwarp();
+        fold_tile<kRegLow>(s_cl, m, static_cast<unsigned>(tn), lane, s_act, nconst, npad);
+        count_active(s_act, npad, 1u << lane, pl);
+      }
     }
   }
   if (lane == 0) {
@@ -501,9 +526,48 @@ static cudaError_t launch_sp_tma(const LaunchCtx& lc, float2* psi, int n, int a1
   return launch_sp_tma_c<Q, C0>(lc, psi, n, a1, a2, mode, brow, err);
 }
 
+// The stored counts of every tile (layout Y), computed once per instance.
+__global__ void __launch_bounds__(kLpTmaWarps * 32)
+    lp_counts_kernel(int m, const ClauseLP* __restrict__ cl, unsigned* __restrict__ counts, long long ntiles) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint2* s_act = reinterpret_cast<uint2*>(smem + 16u * m) + warp * (m + 16);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
+  __syncthreads();
+  for (long long tile = static_cast<long long>(blockIdx.x) * kLpTmaWarps + warp; tile < ntiles;
+       tile += static_cast<long long>(gridDim.x) * kLpTmaWarps) {
+    int nconst, npad;
+    unsigned pl[kPlanes];
+    __syncwarp();
+    fold_tile<true>(s_cl, m, static_cast<unsigned>(tile), lane, s_act, nconst, npad);
+    count_active(s_act, npad, 1u << lane, pl);
+    unsigned* c = counts + static_cast<size_t>(tile) * (kCountWords * 32) + lane;
+#pragma unroll
+    for (int b = 0; b < kPlanes; ++b) c[32 * b] = pl[b];
+    c[32 * kPlanes] = static_cast<unsigned>(nconst);
+  }
+}
+
+size_t lp_counts_bytes(int n) {
+  return n > kLowBits ? (static_cast<size_t>(1) << (n - kLowBits)) * kCountWords * 32 * sizeof(unsigned) : 0;
+}
+
+cudaError_t launch_lp_counts(const LaunchCtx& lc, unsigned* counts, int n, int m, const ClauseLP* cl) {
+  const long long ntiles = 1ll << (n - kLowBits);
+  const size_t smem = 16u * static_cast<size_t>(m) + static_cast<size_t>(kLpTmaWarps) * 8u * (m + 16);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(lp_counts_kernel),
+                             16u * QAA_MAX_CLAUSES_DEV + static_cast<size_t>(kLpTmaWarps) * 8u * (QAA_MAX_CLAUSES_DEV + 16));
+  if (e != cudaSuccess) return e;
+  long long grid = (ntiles + kLpTmaWarps - 1) / kLpTmaWarps;
+  if (grid > 4ll * lc.num_sms) grid = 4ll * lc.num_sms;
+  lp_counts_kernel<<<static_cast<unsigned>(grid), kLpTmaWarps * 32, smem, lc.stream>>>(m, cl, counts, ntiles);
+  return cudaGetLastError();
+}
+
 template <int KIND>
 static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl,
-                                 const float2* prow, const float2* brow, int* err) {
+                                 const float2* prow, const float2* brow, int* err, const unsigned* counts) {
   const long long ntiles = 1ll << (n - kLowBits);
   const LpTmaLayout L(m);
   auto kern = lp_tma_kernel<KIND>;
@@ -517,21 +581,21 @@ static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m,
   const long long need = (ntiles + kLpTmaWarps - 1) / kLpTmaWarps;
   if (grid > need) grid = need;
   kern<<<static_cast<unsigned>(grid), kLpTmaWarps * 32, L.total, lc.stream>>>(psi, m, cl, prow, brow, n, ntiles,
-                                                                              err);
+                                                                              err, counts);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
-                            const float2* ptab, const float2* btab, int* err) {
+                            const float2* ptab, const float2* btab, int* err, const unsigned* counts) {
   const int c_req = p.run_c;
   const float2* prow = ptab + static_cast<size_t>(p.prow) * (m + 1);
   const float2* brow = btab + static_cast<size_t>(p.brow) * (n + 1);
   switch (p.kind) {
-    case kLpFirst: return launch_lp_tma<kLpFirst>(lc, psi, n, m, cl, prow, nullptr, err);
-    case kLpMerge: return launch_lp_tma<kLpMerge>(lc, psi, n, m, cl, prow, nullptr, err);
-    case kLpLast: return launch_lp_tma<kLpLast>(lc, psi, n, m, cl, prow, nullptr, err);
-    case kLpPhase: return launch_lp_tma<kLpPhase>(lc, psi, n, m, cl, prow, nullptr, err);
-    case kLpRot: return launch_lp_tma<kLpRot>(lc, psi, n, m, cl, prow, brow, err);
+    case kLpFirst: return launch_lp_tma<kLpFirst>(lc, psi, n, m, cl, prow, nullptr, err, nullptr);
+    case kLpMerge: return launch_lp_tma<kLpMerge>(lc, psi, n, m, cl, prow, nullptr, err, counts);
+    case kLpLast: return launch_lp_tma<kLpLast>(lc, psi, n, m, cl, prow, nullptr, err, counts);
+    case kLpPhase: return launch_lp_tma<kLpPhase>(lc, psi, n, m, cl, prow, nullptr, err, nullptr);
+    case kLpRot: return launch_lp_tma<kLpRot>(lc, psi, n, m, cl, prow, brow, err, counts);
     case kSpW:
     case kSpWBW:
     case kSpRot: {

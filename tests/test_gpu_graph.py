@@ -127,3 +127,16 @@ def test_launch_mode_argument_checks(env):
             inst.set_launch_mode(2)
         inst.set_launch_mode(1)
         inst.set_launch_mode(0)
+
+
+@pytest.mark.parametrize("n,K", [(16, 9), (21, 5), (24, 3)])
+@pytest.mark.parametrize("variant", [0, 3], ids=["wbw", "rotation"])
+def test_stored_clause_counts_are_bit_identical(env, monkeypatch, n, K, variant):
+    """The merged low passes read per-tile counts stored once per handle
+    (QAA_LP_COUNTS=0 recounts every step): the same E(x), the same state."""
+    q, torch = env
+    cl = satgen.planted_instance(n, 30 + n)["clauses"]
+    a = run(q, torch, n, cl, 0, lambda i, p: i.evolve(p, 0.2 * K, K), variant=variant)
+    monkeypatch.setenv("QAA_LP_COUNTS", "0")
+    b = run(q, torch, n, cl, 0, lambda i, p: i.evolve(p, 0.2 * K, K), variant=variant)
+    assert torch.equal(a, b)
