@@ -84,7 +84,9 @@ int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out);
 /* Release the handle and its device tables.  NULL is accepted. */
 int qaa_destroy(qaa_handle h);
 
-/* Bind a cudaStream_t (as void*) for all later work of this handle; NULL = default stream. */
+/* Bind a cudaStream_t (as void*) for all later work of this handle; NULL = default
+ * stream.  Switching to a different stream first waits for the handle's work on
+ * the old one (the handle's device tables are reused across calls). */
 int qaa_set_stream(qaa_handle h, void* cuda_stream);
 
 /*

@@ -432,7 +432,15 @@ int qaa_destroy(qaa_handle h) {
 
 int qaa_set_stream(qaa_handle h, void* cuda_stream) {
   if (!h) return fail(QAA_E_ARG, "null handle");
-  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  const cudaStream_t next = static_cast<cudaStream_t>(cuda_stream);
+  if (next != h->stream) {
+    // the handle's tables, counts and scratch are reused by the next call: the
+    // old stream's work on them must be done before another stream touches them
+    int st = check_handle(h);
+    if (st) return st;
+    QAA_CK(cudaStreamSynchronize(h->stream));
+  }
+  h->stream = next;
   return QAA_OK;
 }
 
