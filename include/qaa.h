@@ -105,8 +105,13 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream);
  *               round trips per step instead of 2g - 2 (3 instead of 4 at
  *               n = 30).  Same Strang step, FP32 butterflies; needs the TMA
  *               passes (QAA_E_ARG otherwise).
- *   q        reserved for the qubits-per-pass choice; only 0 (automatic).
- * Returns QAA_E_ARG for an unknown kind or q != 0.
+ *   q        qubits per strided pass: 0 = automatic (the plan qaa_autotune
+ *            recorded for n, else the default: the fewest groups of at most 11
+ *            bits); 5..11 = the fewest strided groups of at most q bits each
+ *            (the 10 low bits always form one pass; 11 needs the TMA FP32
+ *            passes, the tensor-core variants stop at 10).
+ * Returns QAA_E_ARG for an unknown kind, a q outside those ranges, or a q for
+ * which the n - 10 strided bits have no split into groups of 5..q bits.
  */
 int qaa_set_variant(qaa_handle h, int wht_kind, int q);
 

@@ -448,10 +448,22 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   if (wht_kind < 0 || wht_kind > 3)
     return fail(QAA_E_ARG, "unknown wht_kind (0 = FP32, 1 = BF16x3, 2 = BF16x2, 3 = rotation form)");
-  if (q != 0) return fail(QAA_E_ARG, "only automatic qubits-per-pass (q = 0) is available");
+  const int widest = (wht_kind == 1 || wht_kind == 2 || !h->plan.use_tma) ? 10 : 11;  // 11-bit tiles: TMA FP32 only
+  if (q != 0 && (q < 5 || q > widest))
+    return fail(QAA_E_ARG, "q (qubits per strided pass) must be 0 (automatic) or in [5, " + std::to_string(widest) +
+                               "] for this variant");
   if (wht_kind == qaa::kRotationForm && h->n > qaa::kOnchipMaxBits && !h->plan.use_tma)
     return fail(QAA_E_ARG, "the rotation form needs the TMA passes (not available, or QAA_PASSES=classic)");
-  qaa::make_plan(h->n, h->plan, (wht_kind == 1 || wht_kind == 2) ? 10 : 11);  // no 11-bit tensor-core tiles
+  if (q != 0 && h->n > qaa::kOnchipMaxBits) {
+    const int rest = h->n - qaa::kLowBits, ng = (rest + q - 1) / q;
+    if (5 * ng > rest)
+      return fail(QAA_E_ARG, "no split of the " + std::to_string(rest) + " strided bits into groups of 5.." +
+                                 std::to_string(q) + " bits");
+  }
+  if (q != 0)
+    qaa::make_default_plan(h->n, h->plan, q);  // groups of at most q bits (the fewest such groups)
+  else
+    qaa::make_plan(h->n, h->plan, widest);
   // a plan made (or tuned) for the other form gets the run lengths of this one
   const bool same_form = (h->plan.wht_kind == qaa::kRotationForm) == (wht_kind == qaa::kRotationForm);
   h->plan.wht_kind = wht_kind;

@@ -328,9 +328,39 @@ def test_rotation_form_range_composes(q, torch):
     inst.close()
 
 
+@pytest.fixture(scope="module")
+def n20_reference():
+    n, T, K = 20, 1.0, 4
+    cl = satgen.load_instance("planted_n20_s0")["clauses"]
+    e = oracle.violated_counts(n, cl)
+    return n, T, K, cl, oracle.evolve_strang(n, cl, T, K, energies=e)
+
+
+@pytest.mark.parametrize("variant", [0, 3], ids=["wbw", "rotation"])
+@pytest.mark.parametrize("qbits,groups", [(5, 2), (7, 2), (10, 1), (11, 1)])
+def test_qubits_per_pass_choice(q, torch, n20_reference, variant, qbits, groups):
+    """set_variant(kind, q): the fewest strided groups of at most q bits (10
+    strided bits at n = 20: 5+5 or one group); the same evolution within the FP32 bar."""
+    n, T, K, cl, ref = n20_reference
+    inst = q.Instance(n, cl)
+    inst.set_variant(variant, qbits)
+    d = inst.describe_plan()
+    assert d.count("group bits") == groups, d
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    inst.init_uniform(psi)
+    inst.evolve(psi, T, K)
+    assert np.max(np.abs(to_np(psi) - ref)) <= AMP_TOL
+    inst.close()
+    with q.Instance(24, [[1, 2, 3]]) as other:
+        with pytest.raises(q.QaaError):
+            other.set_variant(3, 5)  # 14 strided bits: no split into groups of exactly 5
+
+
 def test_variant_argument_checks(q, torch):
     inst = q.Instance(16, [[1, 2, 3]])
     with pytest.raises(q.QaaError):
         inst.set_variant(4)
     with pytest.raises(q.QaaError):
-        inst.set_variant(0, 7)
+        inst.set_variant(0, 4)
+    with pytest.raises(q.QaaError):
+        inst.set_variant(1, 11)  # no 11-bit tensor-core tiles
