@@ -373,9 +373,13 @@ int qaa_poll(qaa_server* s, uint64_t ticket, qaa_result* out);
 /* Cancel a request not yet admitted (QAA_E_STATE once admitted). */
 int qaa_cancel(qaa_server* s, uint64_t ticket);
 int qaa_server_stats(qaa_server* s, qaa_server_info* out);
-/* Host-side fault injection for tests: fault 1 delays the worker thread by
- * param milliseconds once; fault 2 fails the next admitted request (status
- * QAA_E_CUDA) without touching the device. */
+/* Fault injection for tests: fault 1 delays the worker thread by param
+ * milliseconds once; fault 2 fails the next admitted request (status
+ * QAA_E_CUDA) without touching the device; fault 3 starts the next persistent
+ * request (15 <= n <= 17 by default) with a grid barrier that can never
+ * complete: its CTAs give up after the barrier's bounded wait (about a second),
+ * record the error and return, and the request ends with QAA_E_TIMEOUT while
+ * the server and the device stay usable.  No fault traps or faults the GPU. */
 int qaa_server_inject(qaa_server* s, int fault, int param);
 /* Finishes running requests, cancels queued ones, releases everything. */
 int qaa_server_destroy(qaa_server* s);

@@ -10,9 +10,9 @@
 // contiguous amplitudes, 256 threads, so one tile per CTA iteration for every
 // group width Q.
 //
-// The grid barrier spins on a generation counter with an iteration limit; on
-// expiry it records an error word (reported as QAA_E_TIMEOUT) and the kernel
-// returns.  Cooperative launch guarantees that all CTAs are resident.
+// The grid barrier spins on a generation counter with an iteration limit
+// (2^21 polls, about a second); on expiry it records an error word (reported
+// as QAA_E_TIMEOUT) and the kernel returns.  Cooperative launch guarantees that all CTAs are resident.
 #include "device_common.cuh"
 
 namespace qaa {
@@ -49,7 +49,7 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
     } else {
       long long it = 0;
       while (*gen == g) {
-        if (++it > (1ll << 26)) {
+        if (++it > (1ll << 21)) {  // about a second: every pass here takes milliseconds at most
           atomicExch(err, 2);
           s_ok = 0;
           break;

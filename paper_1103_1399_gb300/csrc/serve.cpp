@@ -210,6 +210,7 @@ struct qaa_server {
   long long batches = 0, batched = 0, streamed = 0, peak_used = 0;
   std::atomic<int> inject_delay_ms{0};
   std::atomic<int> inject_fail{0};
+  std::atomic<int> inject_stuck_barrier{0};
   std::string fatal;
 };
 
@@ -344,6 +345,10 @@ cudaError_t issue_persistent(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
   cudaError_t e = upload_tables(s, r, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(r->d_bar, 0, 2 * sizeof(unsigned), st);
+  // injected fault: the arrival count starts at 2^32 - 1, so the first grid
+  // barrier never sees all CTAs arrive; they give up after the bound, record
+  // the error word and return (the request ends with QAA_E_TIMEOUT)
+  if (e == cudaSuccess && s->inject_stuck_barrier.exchange(0)) e = cudaMemsetAsync(r->d_bar, 0xFF, sizeof(unsigned), st);
   if (e == cudaSuccess) e = qaa::launch_init_uniform(lc, r->psi, r->n);
   float2* ptab = r->d_tab;
   float2* btab = r->d_tab + static_cast<size_t>(r->K + 1) * (r->m + 1);
@@ -744,8 +749,11 @@ int qaa_server_inject(qaa_server* s, int fault, int param) {
     s->inject_delay_ms = std::max(param, 0);
   } else if (fault == 2) {
     s->inject_fail = 1;
+  } else if (fault == 3) {
+    s->inject_stuck_barrier = 1;
   } else {
-    return sfail(QAA_E_ARG, "unknown fault (1 = delay the worker, 2 = fail the next admission)");
+    return sfail(QAA_E_ARG,
+                 "unknown fault (1 = delay the worker, 2 = fail the next admission, 3 = stuck grid barrier)");
   }
   s->cv.notify_all();
   return QAA_OK;

@@ -171,3 +171,24 @@ def test_invalid_submissions(env):
             srv.submit(5, [[1, 2, 3]], 1.0, 0)
         with pytest.raises(q.QaaError):
             srv.poll(12345)
+
+
+def test_stuck_grid_barrier_times_out_and_the_server_recovers(env):
+    """A persistent request whose grid barrier can never complete (injected)
+    ends with QAA_E_TIMEOUT after the barrier's bounded wait; requests before
+    and after it, on chip, persistent and streamed, finish correctly."""
+    q, torch = env
+    T, K = 1.0, 10
+    inst = {n: satgen.planted_instance(n, 50 + n)["clauses"] for n in (12, 16, 19)}
+    with q.Server(max_slots=8) as srv:
+        srv.inject(3)
+        bad = srv.submit(16, inst[16], T, K)
+        res = wait_all(srv, [bad], timeout=120.0)
+        assert res[bad]["status"] == -4
+        good = [srv.submit(n, inst[n], T, K) for n in (12, 16, 19)]
+        res = wait_all(srv, good, timeout=120.0)
+    for n, t in zip((12, 16, 19), good):
+        r = res[t]
+        assert r["status"] == 0
+        ref = alone(q, torch, n, inst[n], T, K)
+        assert abs(r["success_prob"] - ref["ground_prob"]) <= 1e-6
