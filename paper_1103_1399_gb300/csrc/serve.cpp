@@ -129,6 +129,8 @@ struct Req {
   int* d_err = nullptr;
   long long chunk = 0;
   unsigned* d_bar = nullptr;
+  unsigned* d_counts = nullptr;  // stored per-tile clause counts (streamed requests), else null
+  size_t counts_bytes = 0;
   cudaEvent_t done_ev = nullptr;
   cudaGraphExec_t gexec = nullptr;  // launch graph of a streamed request, kept until it completes
   bool persist = false;  // mid-size: one persistent cooperative launch for the whole run
@@ -147,8 +149,9 @@ size_t table_bytes(int n, int m, long long K, bool whole_run, bool graph) {
 
 // Device bytes of one request: state, clause tables, phase tables, reduction
 // partials, results, an error word and a grid-barrier word pair.
-size_t request_bytes(int n, int m, size_t tab_bytes, int num_sms) {
+size_t request_bytes(int n, int m, size_t tab_bytes, size_t counts_bytes, int num_sms) {
   size_t b = align_up((static_cast<size_t>(8) << n));
+  b += align_up(counts_bytes);
   b += align_up(16u * static_cast<size_t>(std::max(m, 1))) * 2;
   b += align_up(tab_bytes);
   b += align_up(8u * qaa::obs_partials_len(n, num_sms));
@@ -245,7 +248,7 @@ void release(qaa_server* s, Req* r) {
 bool place(qaa_server* s, Req* r) {
   r->chunk = (r->small() || r->persistent()) ? r->K : std::min(qaa::kChunkSteps, r->K);
   const size_t tb = table_bytes(r->n, r->m, r->K, r->small() || r->persistent(), r->graph);
-  const size_t need = request_bytes(r->n, r->m, tb, s->num_sms);
+  const size_t need = request_bytes(r->n, r->m, tb, r->counts_bytes, s->num_sms);
   if (s->free_slots.empty()) return false;
   size_t off = 0;
   if (!s->arena.alloc(need, &off)) return false;
@@ -267,6 +270,7 @@ bool place(qaa_server* s, Req* r) {
   r->d_res = reinterpret_cast<double*>(take(64));
   r->d_err = reinterpret_cast<int*>(take(16));
   r->d_bar = reinterpret_cast<unsigned*>(take(16));
+  r->d_counts = r->counts_bytes ? reinterpret_cast<unsigned*>(take(r->counts_bytes)) : nullptr;
   return true;
 }
 
@@ -303,6 +307,7 @@ cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
   cudaError_t e = upload_tables(s, r, st);
   if (e == cudaSuccess) e = qaa::launch_init_uniform(lc, r->psi, r->n);
+  if (e == cudaSuccess && r->d_counts) e = qaa::launch_lp_counts(lc, r->d_counts, r->n, r->m, r->d_lp);
   const double dt = r->T / static_cast<double>(r->K);
   if (r->graph) {
     qaa::GraphSpec gs;
@@ -316,6 +321,7 @@ cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
     gs.k0 = 0;
     gs.k1 = r->K;
     gs.num_sms = s->num_sms;
+    gs.counts = r->d_counts;
     qaa::graph_scratch_split(r->d_tab, r->m, gs);
     if (e == cudaSuccess) e = qaa::build_evolve_graph(gs, &r->gexec);
     if (e == cudaSuccess) e = cudaGraphLaunch(r->gexec, st);
@@ -332,7 +338,7 @@ cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
     qaa::build_passes(r->plan, 0, r->K, c0, c1, passes);
     for (const qaa::Pass& ps : passes) {
       if (e != cudaSuccess) break;
-      e = qaa::launch_planned_pass(lc, r->plan, ps, r->psi, r->m, r->d_lp, ptab, btab, r->d_err);
+      e = qaa::launch_planned_pass(lc, r->plan, ps, r->psi, r->m, r->d_lp, ptab, btab, r->d_err, r->d_counts);
     }
   }
   if (e == cudaSuccess) e = observe_async(s, r, st);
@@ -673,12 +679,20 @@ int qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, in
   r->persist = !r->plan.onchip && n <= s->persist_max_bits && steps <= kPersistMaxSteps;
   if (r->persist) qaa::make_plan(n, r->plan, 10);  // the persistent kernel's tiles hold at most 10 bits
   r->graph = !r->plan.onchip && !r->persist && s->use_graphs;
+  // Streamed requests store the per-tile clause counts once (1.375 bytes per
+  // amplitude) so the merged low passes read them instead of counting each step.
+  {
+    const char* env = std::getenv("QAA_LP_COUNTS");
+    if (!r->plan.onchip && !r->persist && r->plan.use_tma && n > qaa::kOnchipMaxBits && !(env && std::atoi(env) == 0))
+      r->counts_bytes = qaa::lp_counts_bytes(n);
+  }
   if (r->plan.onchip && qaa::onchip_smem_bytes(n, m) > 227u * 1024u) {
     delete r;
     return sfail(QAA_E_ARG, "instance too large for the on-chip evolver");
   }
   const size_t need =
-      request_bytes(n, m, table_bytes(n, m, steps, r->plan.onchip || r->persist, r->graph), s->num_sms);
+      request_bytes(n, m, table_bytes(n, m, steps, r->plan.onchip || r->persist, r->graph), r->counts_bytes,
+                    s->num_sms);
   if (need > s->arena.size()) {
     delete r;
     return sfail(QAA_E_NOMEM, "request needs " + std::to_string(need) + " device bytes, more than the server's " +
