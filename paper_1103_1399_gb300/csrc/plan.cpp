@@ -313,7 +313,7 @@ std::string describe_plan(const PassPlan& plan) {
       const Group& g = plan.strided[i];
       d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";
       if (g.q > 5) d += "+[" + std::to_string(g.a2) + "," + std::to_string(g.a2 + g.q - 5) + ")";
-      d += plan.run_c[i] == 4 ? " R 128B runs" : " R 64B runs";
+      d += " R " + std::to_string(tma_run_bytes(g.q, plan.run_c[i])) + "B runs";
     }
     return d + "; " + std::to_string(ng + 1) + " HBM round trips per step";
   }
@@ -325,7 +325,7 @@ std::string describe_plan(const PassPlan& plan) {
     d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";
     if (g.q > 5) d += "+[" + std::to_string(g.a2) + "," + std::to_string(g.a2 + g.q - 5) + ")";
     d += i == plan.phase_group ? " W.B.W" : " W";
-    if (plan.use_tma && !plan.wht_kind) d += plan.run_c[i] == 4 ? " 128B runs" : " 64B runs";
+    if (plan.use_tma && !plan.wht_kind) d += " " + std::to_string(tma_run_bytes(g.q, plan.run_c[i])) + "B runs";
   }
   d += "; " + std::to_string(2 * ng) + " HBM round trips per step";
   return d;

@@ -124,6 +124,8 @@ cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, in
 bool tma_available();
 // counts (optional): the stored per-tile violated-clause counts of
 // launch_lp_counts, read by the merged low passes instead of counting again.
+// Bytes per contiguous tile row of a q-bit TMA strided pass (run_c as in Pass).
+int tma_run_bytes(int q, int run_c);
 cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
                             const float2* ptab, const float2* btab, int* err, const unsigned* counts = nullptr);
 // Per-tile bit-sliced violated-clause counts of every 1024-amplitude tile

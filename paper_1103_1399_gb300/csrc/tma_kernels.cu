@@ -526,6 +526,11 @@ static cudaError_t launch_sp_tma(const LaunchCtx& lc, float2* psi, int n, int a1
   return launch_sp_tma_c<Q, C0>(lc, psi, n, a1, a2, mode, brow, err);
 }
 
+int tma_run_bytes(int q, int run_c) {
+  const int c = (q <= 10 && run_c == 4 && tma_c(q) < 4) ? 4 : tma_c(q);
+  return 8 << c;
+}
+
 // The stored counts of every tile (layout Y), computed once per instance.
 __global__ void __launch_bounds__(kLpTmaWarps * 32)
     lp_counts_kernel(int m, const ClauseLP* __restrict__ cl, unsigned* __restrict__ counts, long long ntiles) {
