@@ -183,6 +183,7 @@ int prof_kind(int pass_kind) {
   switch (pass_kind) {
     case qaa::kLpPhase: return QAA_K_LOW_FIRST;
     case qaa::kLpRot: return QAA_K_LOW_MERGE;
+    case qaa::kLpRot12: return QAA_K_LOW_MERGE;
     case qaa::kSpRot: return QAA_K_STRIDED;
     default: return pass_kind;
   }
@@ -468,6 +469,8 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   const bool same_form = (h->plan.wht_kind == qaa::kRotationForm) == (wht_kind == qaa::kRotationForm);
   h->plan.wht_kind = wht_kind;
   if (!same_form) qaa::set_default_run_c(h->plan);
+  // only the rotation form has a 12-bit low pass
+  if (wht_kind != qaa::kRotationForm) qaa::narrow_low_pass(h->plan, q != 0 ? q : widest);
   return QAA_OK;
 }
 
@@ -479,7 +482,10 @@ namespace {
 // tensor-core variant keeps that variant.
 double time_plan(qaa_ctx* h, float2* psi, const qaa::PassPlan& plan, int steps, int tc_kind) {
   h->plan = plan;
-  if (tc_kind) h->plan.wht_kind = tc_kind;
+  if (tc_kind) {
+    h->plan.wht_kind = tc_kind;
+    qaa::narrow_low_pass(h->plan, 10);
+  }
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
     cudaGetLastError();
@@ -575,21 +581,21 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
   if (best.use_tma && best.strided.size() == 2 && best.strided[0].q == best.strided[1].q && best.strided[0].q >= 10 &&
       spent() <= budget_ms) {
     qaa::PassPlan c = best;
-    const int q = c.strided[0].q;
+    const int q = c.strided[0].q, L = c.low_bits;
     const bool split = c.strided[0].a2 != c.strided[0].a + 5;
     if (split) {
-      c.strided[0] = {qaa::kLowBits, q, qaa::kLowBits + 5};
-      c.strided[1] = {qaa::kLowBits + q, q, qaa::kLowBits + q + 5};
+      c.strided[0] = {L, q, L + 5};
+      c.strided[1] = {L + q, q, L + q + 5};
     } else {
-      c.strided[0] = {qaa::kLowBits, q, qaa::kLowBits + q + 5};
-      c.strided[1] = {qaa::kLowBits + 5, q, qaa::kLowBits + 10};
+      c.strided[0] = {L, q, L + q + 5};
+      c.strided[1] = {L + 5, q, L + 10};
     }
     consider(c);
   }
   // stage 4: plain loads instead of TMA (groups of at most 10 bits, contiguous)
   bool narrow = true;
   for (const auto& g : best.strided) narrow = narrow && g.q <= 10;
-  if (best.use_tma && narrow && spent() <= budget_ms) {
+  if (best.use_tma && narrow && best.low_bits == qaa::kLowBits && spent() <= budget_ms) {
     qaa::PassPlan c = best;
     c.use_tma = false;
     c.wht_kind = 0;  // plain loads: the W.B.W form only
@@ -617,7 +623,10 @@ int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* rep
       }
   }
   h->plan = best;
-  if (tc_kind) h->plan.wht_kind = tc_kind;
+  if (tc_kind) {
+    h->plan.wht_kind = tc_kind;
+    qaa::narrow_low_pass(h->plan, 10);
+  }
   qaa::PassPlan rec = best;
   qaa::set_tuned_plan(rec);
   h->prof = prof;

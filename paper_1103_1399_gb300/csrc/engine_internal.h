@@ -31,6 +31,7 @@ struct PassPlan {
   std::vector<Group> strided;  // ascending bit order
   int phase_group = 0;         // strided group whose pass fuses W B W
   std::vector<int> run_c;      // per strided group: 4 = 128-byte runs, 0 = default
+  int low_bits = kLowBits;     // bits of the low pass: 10, or 12 (rotation form, kLpRot12)
 };
 
 // Plan for n: the one qaa_autotune chose for n on the current device, if any
@@ -39,16 +40,21 @@ struct PassPlan {
 // plain-load and tensor-core passes, which have no 11-bit tiles).
 void make_plan(int n, PassPlan& plan, int max_q = 11);
 // Default plan for n, with the tuning overrides QAA_PASSES, QAA_SPLIT_GROUPS,
-// QAA_PHASE_GROUP, QAA_RUN128_GROUPS and QAA_GROUP_BITS read from the
-// environment.
-void make_default_plan(int n, PassPlan& plan, int max_q = 11);
+// QAA_PHASE_GROUP, QAA_RUN128_GROUPS, QAA_GROUP_BITS and QAA_LOW_BITS read
+// from the environment.  low: bits of the low pass, 10 or 12 (12 only for the
+// rotation form on TMA passes); 0 = QAA_LOW_BITS, else 10.
+void make_default_plan(int n, PassPlan& plan, int max_q = 11, int low = 0);
 // Run lengths per group for the plan's form (QAA_RUN128_GROUPS overrides).
 void set_default_run_c(PassPlan& plan);
+// A plan with a 12-bit low pass becomes the default plan with a 10-bit one
+// (same form): for the W.B.W, tensor-core and plain-load passes.
+void narrow_low_pass(PassPlan& plan, int max_q = 11);
 
 // Autotuner support.  First-stage candidates for n >= 15: the default plan,
 // then every split of bits 10..n-1 into the fewest groups of 5..11 bits (5..10
 // without TMA; the fewest HBM round trips) with every choice of phase group;
-// run lengths 128 B for plain groups and 64 B for the phase group.
+// run lengths 128 B for plain groups and 64 B for the phase group; for
+// n >= 31 on TMA passes, last, the rotation form with a 12-bit low pass.
 void plan_candidates(int n, std::vector<PassPlan>& out);
 // Contiguous groups of the given widths from bit 10 up.
 void plan_with_groups(int n, const std::vector<int>& sizes, int phase_group, bool tma, PassPlan& plan);

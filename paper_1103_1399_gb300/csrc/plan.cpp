@@ -73,7 +73,8 @@ std::mutex g_tuned_mu;
 std::map<std::pair<int, int>, PassPlan> g_tuned;  // (device, n) -> plan chosen by qaa_autotune
 
 bool env_overrides() {
-  for (const char* v : {"QAA_PASSES", "QAA_GROUP_BITS", "QAA_SPLIT_GROUPS", "QAA_PHASE_GROUP", "QAA_RUN128_GROUPS"})
+  for (const char* v :
+       {"QAA_PASSES", "QAA_GROUP_BITS", "QAA_SPLIT_GROUPS", "QAA_PHASE_GROUP", "QAA_RUN128_GROUPS", "QAA_LOW_BITS"})
     if (std::getenv(v)) return true;
   return false;
 }
@@ -157,6 +158,12 @@ void plan_candidates(int n, std::vector<PassPlan>& out) {
                p.strided[i].a2 == def.strided[i].a2;
       if (!same) out.push_back(p);
     }
+  // the rotation form with a 12-bit low pass (kLpRot12), for states beyond L2
+  if (tma && n >= 31) {
+    PassPlan w;
+    make_default_plan(n, w, max_q, 12);
+    if (w.low_bits == 12 && def.low_bits != 12) out.push_back(w);
+  }
 }
 
 static bool fits(const PassPlan& plan, int max_q) {
@@ -170,7 +177,7 @@ void make_plan(int n, PassPlan& plan, int max_q) {
   make_default_plan(n, plan, max_q);
 }
 
-void make_default_plan(int n, PassPlan& plan, int max_q) {
+void make_default_plan(int n, PassPlan& plan, int max_q, int low) {
   plan = PassPlan();
   plan.n = n;
   plan.onchip = n <= kOnchipMaxBits;
@@ -178,7 +185,19 @@ void make_default_plan(int n, PassPlan& plan, int max_q) {
   plan.use_tma = tma_available() && !(env && std::strcmp(env, "classic") == 0);
   if (plan.onchip) return;
   if (!plan.use_tma && max_q > 10) max_q = 10;  // 11-bit groups: TMA FP32 passes only
-  const int rest = n - kLowBits;
+  // Low pass width: 10 bits, or 12 (kLpRot12, rotation form on TMA passes
+  // only) when asked for here or by QAA_LOW_BITS.  Not the default: at n = 32
+  // its two 10-bit groups with 128-byte runs ran 0.87 ms faster each than the
+  // two 11-bit groups with 64-byte runs, but the 12-bit low pass itself took
+  // 13.8 ms against 11.7 (its warp quads run in step and hide less latency):
+  // 36.3 against 35.9 ms per step.  The autotuner offers it for n >= 31.
+  if (low == 0) {
+    const char* lb = std::getenv("QAA_LOW_BITS");
+    low = lb ? std::atoi(lb) : kLowBits;
+  }
+  const int L = (low == 12 && plan.use_tma && n - 12 >= 5) ? 12 : kLowBits;
+  plan.low_bits = L;
+  const int rest = n - L;
   std::vector<int> sizes;
   if (const char* gb = std::getenv("QAA_GROUP_BITS")) {
     int sum = 0;
@@ -198,7 +217,7 @@ void make_default_plan(int n, PassPlan& plan, int max_q) {
     const int base = rest / ng, extra = rest % ng;
     for (int g = 0; g < ng; ++g) sizes.push_back(base + (g < extra ? 1 : 0));
   }
-  int a = kLowBits;
+  int a = L;
   for (int q : sizes) {
     plan.strided.push_back({a, q, a + 5});
     a += q;
@@ -212,8 +231,8 @@ void make_default_plan(int n, PassPlan& plan, int max_q) {
   const bool split = plan.use_tma && !(sg && std::atoi(sg) == 0);
   if (split && plan.strided.size() == 2 && plan.strided[0].q == plan.strided[1].q && plan.strided[0].q >= 10) {
     const int q = plan.strided[0].q;
-    plan.strided[0] = {kLowBits, q, kLowBits + q + 5};
-    plan.strided[1] = {kLowBits + 5, q, kLowBits + 10};
+    plan.strided[0] = {L, q, L + q + 5};
+    plan.strided[1] = {L + 5, q, L + 10};
   }
   const int ng = static_cast<int>(plan.strided.size());
   plan.phase_group = ng - 1;
@@ -225,6 +244,14 @@ void make_default_plan(int n, PassPlan& plan, int max_q) {
   // (W.diag.W on every 5-qubit block inside each pass: g round trips per
   // step), otherwise the W.B.W form (2g - 2).
   plan.wht_kind = plan.use_tma ? kRotationForm : 0;
+  set_default_run_c(plan);
+}
+
+void narrow_low_pass(PassPlan& plan, int max_q) {
+  if (plan.onchip || plan.low_bits == kLowBits) return;
+  const int wk = plan.wht_kind;
+  make_default_plan(plan.n, plan, max_q, kLowBits);
+  plan.wht_kind = wk;
   set_default_run_c(plan);
 }
 
@@ -262,7 +289,7 @@ static void build_rot_passes(const PassPlan& plan, long long k0, long long c0, l
       const Group& g = plan.strided[i];
       out.push_back({kSpRot, g.a, g.q, 0, plan.run_c[i], brow, g.a2});
     }
-    out.push_back({kLpRot, 0, 0, static_cast<int>(k + 1 - c0), 0, brow, 0});
+    out.push_back({plan.low_bits == 12 ? kLpRot12 : kLpRot, 0, 0, static_cast<int>(k + 1 - c0), 0, brow, 0});
   }
 }
 
@@ -308,7 +335,8 @@ std::string describe_plan(const PassPlan& plan) {
   if (plan.onchip) return "on-chip: whole run in one CTA's shared memory (n=" + std::to_string(plan.n) + ")";
   const int ng = static_cast<int>(plan.strided.size());
   if (plan.wht_kind == kRotationForm) {
-    std::string d = "streaming, TMA loads, rotation form (H_B per 5-qubit block: W.diag.W); low pass bits [0,10) R.P";
+    std::string d = "streaming, TMA loads, rotation form (H_B per 5-qubit block: W.diag.W); low pass bits [0," +
+                    std::to_string(plan.low_bits) + ") R.P";
     for (int i = 0; i < ng; ++i) {
       const Group& g = plan.strided[i];
       d += "; group bits [" + std::to_string(g.a) + "," + std::to_string(g.a + 5) + ")";

@@ -54,6 +54,7 @@ enum PassKind : int {
   kLpPhase = 5,  // psi <- P(prow) psi                     (first pass of a range)
   kLpRot = 6,    // psi <- 2^-n P(prow) R_G1(brow) psi     (ends every step)
   kSpRot = 7,    // psi <- R_G(brow) psi over a strided group (unnormalised by 2^q)
+  kLpRot12 = 8,  // kLpRot over bits 0..11: four 1024-amplitude tiles per warp quad
 };
 
 struct Pass {

@@ -677,7 +677,10 @@ int qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, in
   // Persistent launches keep the phase tables of the whole run resident, so
   // they take runs of at most kPersistMaxSteps steps.
   r->persist = !r->plan.onchip && n <= s->persist_max_bits && steps <= kPersistMaxSteps;
-  if (r->persist) qaa::make_plan(n, r->plan, 10);  // the persistent kernel's tiles hold at most 10 bits
+  if (r->persist) {
+    qaa::make_plan(n, r->plan, 10);  // the persistent kernel's tiles hold at most 10 bits
+    qaa::narrow_low_pass(r->plan, 10);
+  }
   r->graph = !r->plan.onchip && !r->persist && s->use_graphs;
   // Streamed requests store the per-tile clause counts once (1.375 bytes per
   // amplitude) so the merged low passes read them instead of counting each step.

@@ -331,6 +331,52 @@ __device__ __forceinline__ void load_counts(const unsigned* __restrict__ counts,
   nconst = static_cast<int>(__ldg(c + 32 * kPlanes));
 }
 
+// Warp quads (kLpRot12): warps 4k..4k+3 of a CTA sync on named barrier 1 + k
+// (immediate ids, so that only barriers 0..2 are reserved).
+template <int ID>
+__device__ __forceinline__ bool quad_any_id(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(v)), "n"(ID)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ bool quad_any(bool v, int quad) { return quad ? quad_any_id<2>(v) : quad_any_id<1>(v); }
+__device__ __forceinline__ void quad_sync(int quad) {
+  if (quad)
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+  else
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// exp(-i theta H_B) on index bits 10 and 11 of four 1024-amplitude tiles held
+// in the quad's shared buffers (tile k of the quad = bits 10..11 equal to k):
+// W diag(exp(-i theta popcount)) W on the two bits, up to the factor 4.
+__device__ __forceinline__ void quad_rot2(float2* const (&b)[4], const float2 (&tab)[6], int t) {
+#pragma unroll 2
+  for (int o = t; o < 1024; o += 128) {
+    float2 a0 = b[0][o], a1 = b[1][o], a2 = b[2][o], a3 = b[3][o];
+    butterfly(a0, a1);
+    butterfly(a2, a3);
+    butterfly(a0, a2);
+    butterfly(a1, a3);
+    a0 = cmul(a0, tab[0]);
+    a1 = cmul(a1, tab[1]);
+    a2 = cmul(a2, tab[1]);
+    a3 = cmul(a3, tab[2]);
+    butterfly(a0, a1);
+    butterfly(a2, a3);
+    butterfly(a0, a2);
+    butterfly(a1, a3);
+    b[0][o] = a0;
+    b[1][o] = a1;
+    b[2][o] = a2;
+    b[3][o] = a3;
+  }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     lp_tma_kernel(float2* __restrict__ psi, int m, const ClauseLP* __restrict__ cl, const float2* __restrict__ prow,
@@ -360,11 +406,19 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
   }
   for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
   // the rotation form's last pass of a step also removes the 2^n of its rotations (exact)
-  const float psc = KIND == kLpRot ? ldexpf(1.0f, -n) : 1.0f;
+  constexpr bool kRot = KIND == kLpRot || KIND == kLpRot12;
+  constexpr bool kQuad = KIND == kLpRot12;
+  const float psc = kRot ? ldexpf(1.0f, -n) : 1.0f;
   for (int i = threadIdx.x; i <= m; i += blockDim.x) s_pt[i] = make_float2(prow[i].x * psc, prow[i].y * psc);
   float2 rtab[6];
 #pragma unroll
-  for (int p = 0; p < 6; ++p) rtab[p] = KIND == kLpRot ? brow[p] : make_float2(0.f, 0.f);
+  for (int p = 0; p < 6; ++p) rtab[p] = kRot ? brow[p] : make_float2(0.f, 0.f);
+  // kLpRot12: the quad's four tile buffers (tile first + k of the quad in warp 4q + k's buffer)
+  const int quad = warp >> 2;
+  float2* qbuf[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    qbuf[k] = reinterpret_cast<float2*>(smem + L.off_warp + L.per_warp * (4 * quad + k));
   __syncthreads();
 
   int nconst = 0, npad = 0;
@@ -381,9 +435,16 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
   int it = 0;
   for (long long tile = first; tile < ntiles; tile += step, ++it) {
     const bool ok = mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u);
-    if (__any_sync(0xffffffffu, !ok)) {
+    // a quad leaves together (its four warps have the same tiles left)
+    if (kQuad ? quad_any(!ok, quad) : __any_sync(0xffffffffu, !ok)) {
       if (lane == 0) atomicExch(err, kErrTimeout);
       break;
+    }
+    if (kQuad) {
+      // all four tiles are in (the barrier above): bits 10..11 across them
+      quad_rot2(qbuf, rtab, threadIdx.x & 127);
+      fence_proxy_async();  // these writes precede the next bulk copies into the buffers
+      quad_sync(quad);
     }
     float2 v[32];
     {
@@ -394,7 +455,7 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     __syncwarp();
     if (KIND == kLpPhase) {
       apply_p_phase(v, pl, nconst, s_pt);
-    } else if (KIND == kLpRot) {
+    } else if (kRot) {
       reg_rot<5>(v, rtab);
       xpose_x2y_t(v, s_buf, lane);
       reg_rot<5>(v, rtab);
@@ -601,6 +662,9 @@ cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int
     case kLpLast: return launch_lp_tma<kLpLast>(lc, psi, n, m, cl, prow, nullptr, err, counts);
     case kLpPhase: return launch_lp_tma<kLpPhase>(lc, psi, n, m, cl, prow, nullptr, err, nullptr);
     case kLpRot: return launch_lp_tma<kLpRot>(lc, psi, n, m, cl, prow, brow, err, counts);
+    case kLpRot12:
+      if (n < 12) return cudaErrorInvalidValue;
+      return launch_lp_tma<kLpRot12>(lc, psi, n, m, cl, prow, brow, err, counts);
     case kSpW:
     case kSpWBW:
     case kSpRot: {

@@ -105,14 +105,18 @@ def test_autotune_candidates_cover_every_split(q, n):
     rest = n - 10
     g = (rest + 9) // 10
     full = _compositions(rest, g) * g
-    # the default plan comes first; when it is one of the contiguous splits it is not repeated
-    assert len(descs) in (full, full + 1)
+    # the default plan comes first; when it is one of the contiguous splits it is
+    # not repeated; with TMA passes, n >= 31 adds a 12-bit low pass candidate
+    wide = [d for d in descs if "low pass bits [0,12)" in d]
+    assert len(wide) == 0 or n >= 31
+    assert len(descs) - len(wide) in (full, full + 1)
     assert len(set(descs)) == len(descs)
     widths = set()
     for d in descs:
         bits, phase = _group_bits(d)
-        assert bits == list(range(10, n)), d  # every bit above the low pass exactly once
-        assert phase == 1, d
+        low = 12 if d in wide else 10
+        assert bits == list(range(low, n)), d  # every bit above the low pass exactly once
+        assert phase == (0 if "rotation form" in d else 1), d  # W.B.W: one phase group
         widths.add(tuple(int(b) - int(a) for a, b in re.findall(r"group bits \[(\d+),(\d+)\)", d)))
     # every first-half width 5 appears: e.g. n = 25 offers 5+10, 6+9, ..., 10+5
     assert len(descs) >= _compositions(rest, g)
