@@ -314,8 +314,9 @@ __device__ __forceinline__ void xpose_y2x_t(float2 (&v)[32], float2* __restrict_
   __syncwarp();
 }
 
-// KIND kLpPhase / kLpRot: the rotation form (P alone; the rotations of bits
-// 0..9 then 2^-n P), with B row entries 0..5 = exp(-i theta p).
+// KIND kLpPhase / kLpRot / kLpRot12: the rotation form (P alone; the
+// rotations of bits 0..9, or 0..11 with warp quads, then 2^-n P), with B row
+// entries 0..5 = exp(-i theta p).
 // Stored per-tile counts (layout Y: registers hold bits 0..4): for tile t and
 // lane l, word (t * kCountWords + b) * 32 + l holds bit plane b of the lane's 32
 // violated-clause counts (b < kPlanes), and word kPlanes the tile's constant
