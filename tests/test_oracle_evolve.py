@@ -217,3 +217,43 @@ def test_order4_converges_at_fourth_order_time_dependent_sat():
     # and it beats Strang at equal work (3 Strang sub-steps per fourth-order step)
     strang = np.max(np.abs(oracle.evolve_strang(n, cl, T, 120) - ref))
     assert errs[1] < strang
+
+
+def _time_ordered_reference(n, clauses, T, psi0):
+    """The Schroedinger equation i dpsi/dt = H(t/T) psi of Eq. (1) integrated
+    directly (scipy's DOP853 at 1e-12 tolerances): the time-ordered propagator,
+    independent of any step schedule."""
+    import scipy.integrate
+    from oracle.hamiltonian import h_dense
+    hb = h_dense(n, clauses, 0.0)
+    hp = h_dense(n, clauses, 1.0)
+
+    def rhs(t, y):
+        s = t / T
+        return -1j * (((1.0 - s) * hb + s * hp) @ y)
+
+    sol = scipy.integrate.solve_ivp(rhs, (0.0, T), psi0.astype(complex), method="DOP853", rtol=1e-12, atol=1e-13)
+    assert sol.success
+    return sol.y[:, -1]
+
+
+def test_midpoint_schedule_is_second_order_in_time():
+    """Stepping with H frozen at the step midpoints s_k = (k + 1/2)/K converges
+    to the time-ordered solution at second order (error ratio 4 when dt halves);
+    freezing H at the left end of each step, s = k/K, is only first order
+    (ratio 2), so a schedule off by half a step fails here."""
+    inst = satgen.planted_instance(3, 2)
+    n, cl, T = 3, inst["clauses"], 3.0
+    psi0 = oracle.uniform_state(n)
+    ref = _time_ordered_reference(n, cl, T, psi0)
+    mid, left = [], []
+    for K in (10, 20, 40, 80):
+        mid.append(np.max(np.abs(oracle.evolve_exact(n, cl, T, K) - ref)))
+        left.append(np.max(np.abs(oracle.evolve_exact(n, cl, T, K, s_values=np.arange(K) / K) - ref)))
+    r_mid = [mid[i] / mid[i + 1] for i in range(3)]
+    r_left = [left[i] / left[i + 1] for i in range(3)]
+    assert all(3.6 < r < 4.4 for r in r_mid), r_mid
+    assert all(1.7 < r < 2.3 for r in r_left), r_left
+    # the Strang split with the same schedule is second order to the same solution
+    st = [np.max(np.abs(oracle.evolve_strang(n, cl, T, K) - ref)) for K in (20, 40, 80)]
+    assert all(3.5 < st[i] / st[i + 1] < 4.5 for i in range(2)), st

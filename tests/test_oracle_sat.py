@@ -95,3 +95,28 @@ def test_energy_sum_identity():
     n, m = 10, 57
     cl = satgen.random_instance(n, m, seed=11)
     assert int(oracle.violated_counts(n, cl).sum()) == m * (1 << (n - 3))
+
+
+def test_paper_instance_full_diagonal_and_histogram(paper):
+    # Every one of the 64 energies of the worked instance of Sec. 2.2, and their
+    # histogram.  A clause with a flipped literal sign, a dropped or duplicated
+    # clause, or a transposed bit order changes several entries.
+    e = oracle.violated_counts(paper["n"], paper["clauses"])
+    assert e.tolist() == paper["diagonal"]
+    hist = {str(k): int(v) for k, v in enumerate(np.bincount(e)) if v}
+    assert hist == paper["histogram"]
+    assert sum(paper["histogram"].values()) == 64
+    # each 3-literal clause over distinct variables is violated by 8 of the 64 assignments
+    assert int(e.sum()) == 8 * len(paper["clauses"]) == 216
+
+
+def test_planted_mistakes_change_the_paper_diagonal(paper):
+    # The pin above is sensitive: each plausible slip, planted here in a copy of
+    # the clause list, moves the diagonal away from the stored one.
+    base = [list(c) for c in paper["clauses"]]
+    flipped = [list(c) for c in base]
+    flipped[5][1] = -flipped[5][1]
+    dropped = base[:17] + base[18:]
+    reversed_bits = [[(7 - abs(l)) * (1 if l > 0 else -1) for l in c] for c in base]
+    for cl in (flipped, dropped, reversed_bits):
+        assert oracle.violated_counts(6, cl).tolist() != paper["diagonal"]
