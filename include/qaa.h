@@ -348,6 +348,11 @@ typedef struct {
   double t_submit;       /* seconds on the server's steady clock                   */
   double t_admit;        /* memory granted (-1 if never admitted)                  */
   double t_done;         /* results available                                      */
+  double t_dev_start;    /* the request's device interval, seconds on the device   */
+  double t_dev_end;      /* clock since the server's creation (-1 if not run): from */
+                         /* an event before its first copy or kernel to one after  */
+                         /* its observables' read-back, on the stream it ran on;   */
+                         /* overlapping intervals = requests in flight together    */
   int n;
   int64_t steps;
   int status;            /* QAA_OK, QAA_E_STATE (cancelled), QAA_E_CUDA, QAA_E_TIMEOUT */

@@ -35,7 +35,8 @@ class Obs(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("success_prob", ctypes.c_double), ("energy", ctypes.c_double), ("norm", ctypes.c_double),
                 ("expect_hb", ctypes.c_double), ("ground_count", ctypes.c_int64), ("t_submit", ctypes.c_double),
-                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("n", ctypes.c_int),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("t_dev_start", ctypes.c_double),
+                ("t_dev_end", ctypes.c_double), ("n", ctypes.c_int),
                 ("steps", ctypes.c_int64), ("status", ctypes.c_int)]
 
 

@@ -167,6 +167,21 @@ __device__ __forceinline__ void count_active(const uint2* __restrict__ act, int 
   for (int k = 0; k < kPlanes - 4; ++k) pl[4 + k] = hi[k];
 }
 
+// Stored per-tile counts (layout Y: registers hold bits 0..4): for tile t and
+// lane l, word (t * kCountWords + b) * 32 + l holds bit plane b of the lane's 32
+// violated-clause counts (b < kPlanes), and word kPlanes the tile's constant
+// part.  E(x) never changes during a run, so the merged low passes (and the
+// observables) can read these instead of folding and counting the clauses again.
+constexpr int kCountWords = kPlanes + 1;
+
+__device__ __forceinline__ void load_counts(const unsigned* __restrict__ counts, long long tile, int lane,
+                                            unsigned (&pl)[kPlanes], int& nconst) {
+  const unsigned* c = counts + static_cast<size_t>(tile) * (kCountWords * 32) + lane;
+#pragma unroll
+  for (int b = 0; b < kPlanes; ++b) pl[b] = __ldg(c + 32 * b);
+  nconst = static_cast<int>(__ldg(c + 32 * kPlanes));
+}
+
 // Counts of registers R and R+16 packed as (count_R) | (count_{R+16} << 16).
 template <int R>
 __device__ __forceinline__ unsigned extract_pair(const unsigned (&pl)[kPlanes]) {
@@ -221,6 +236,87 @@ __device__ __forceinline__ void energies(int (&e)[32], const uint2* __restrict__
   unsigned pl[kPlanes];
   count_active(act, npad, lanebit, pl);
   StoreCountUnroll<0>::run(e, pl, nconst);
+}
+
+
+// ---- norm fold (see NormFold) ------------------------------------------------
+// Sum of |v|^2 over a lane's 32 register-held amplitudes: packed FP32 FMAs in
+// two interleaved chains of 16, then one FP32 add per component.
+__device__ __forceinline__ float tile_norm(const float2 (&v)[32]) {
+  unsigned long long a = 0ull, b = 0ull;
+#pragma unroll
+  for (int r = 0; r < 32; r += 2) {
+    const unsigned long long x = f2_bits(v[r]), y = f2_bits(v[r + 1]);
+    asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a) : "l"(x));
+    asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(b) : "l"(y));
+  }
+  const float2 fa = bits_f2(a), fb = bits_f2(b);
+  return (fa.x + fb.x) + (fa.y + fb.y);
+}
+
+// Sum of one slot's partials, in the same fixed order in every CTA: lane i
+// takes partials i, i + 32, ..., then a shuffle tree; lane 0's value is
+// returned to every lane.  Called by one whole warp.
+__device__ __forceinline__ double fold_slot_sum(const double* __restrict__ slot, int lane) {
+  // L2 loads: within a persistent kernel the slot was written by other CTAs
+  // since this SM last read it
+  const int cnt = static_cast<int>(__ldcg(slot));
+  double s = 0.0;
+  for (int i = lane; i < cnt; i += 32) s += __ldcg(slot + 1 + i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
+// The correction factor of a low pass (1 when there is nothing to correct, or
+// when either sum is not a positive finite number), valid in lane 0.  One
+// whole warp calls it; only lane 0 does the scalar FP64 work (GB300's FP64
+// rate is a small fraction of its FP32 rate).
+__device__ __forceinline__ double fold_factor(const NormFold& f, int lane) {
+  if (!f.ref || !f.prev) return 1.0;
+  const double r = fold_slot_sum(f.ref, lane);
+  const double s = fold_slot_sum(f.prev, lane);
+  if (lane != 0) return 1.0;
+  if (!(r > 0.0) || !(s > 0.0) || !isfinite(r) || !isfinite(s)) return 1.0;
+  const double q = r / s;
+  const int j = static_cast<int>(rint(-log2(q)));  // N / N_ref ~ 2^j
+  return sqrt(ldexp(q, j));
+}
+
+// Block-wide correction factor: warp 0 computes it, every thread gets it.
+// Contains a __syncthreads: every thread of the block must call it.
+__device__ __forceinline__ double fold_factor_block(const NormFold& f) {
+  __shared__ double s_c;
+  if (threadIdx.x < 32) {
+    const double c = fold_factor(f, threadIdx.x);
+    if (threadIdx.x == 0) s_c = c;
+  }
+  __syncthreads();
+  return s_c;
+}
+
+// Write the block's partial: the FP64 sum of one value per thread in a fixed
+// order; block 0 also writes the partial count.  Contains __syncthreads:
+// every thread of the block must call it.
+__device__ __forceinline__ void fold_store(const NormFold& f, double v) {
+  __shared__ double s_w[32];
+  if (!f.out) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) s_w[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += s_w[w];
+    f.out[1 + blockIdx.x] = t;
+    if (f.out2) f.out2[1 + blockIdx.x] = t;
+    if (blockIdx.x == 0) {
+      f.out[0] = static_cast<double>(gridDim.x);
+      if (f.out2) f.out2[0] = static_cast<double>(gridDim.x);
+    }
+  }
 }
 
 }  // namespace qaa

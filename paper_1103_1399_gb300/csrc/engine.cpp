@@ -52,6 +52,7 @@ struct qaa_ctx {
   double* d_res = nullptr;
   double* h_res = nullptr;  // pinned
   int* d_err = nullptr;     // set by kernels whose bounded waits expired
+  double* d_fold = nullptr; // norm-fold slots of the low passes (kFoldBytes)
   qaa::PassPlan plan;
   // launch graphs (QAA_LAUNCH_GRAPH): the last built graph and what it was built for
   int launch_mode = QAA_LAUNCH_PASSES;
@@ -194,7 +195,9 @@ int prof_kind(int pass_kind) {
 const unsigned* stored_counts(qaa_ctx* h) {
   if (h->counts_state == 0) {
     const char* env = std::getenv("QAA_LP_COUNTS");
-    const bool want = h->plan.use_tma && h->n > qaa::kOnchipMaxBits && !(env && std::atoi(env) == 0);
+    // the tensor-core variant's low passes read the stored counts whatever QAA_LP_COUNTS says
+    const bool tc = h->plan.wht_kind == 1 || h->plan.wht_kind == 2;
+    const bool want = h->n > qaa::kOnchipMaxBits && (tc || (h->plan.use_tma && !(env && std::atoi(env) == 0)));
     h->counts_state = -1;
     if (want && cudaMalloc(&h->d_counts, qaa::lp_counts_bytes(h->n)) == cudaSuccess) {
       if (qaa::launch_lp_counts(lctx(h), h->d_counts, h->n, h->m, h->d_lp) == cudaSuccess) {
@@ -239,6 +242,7 @@ int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, 
     gs.s_dev = s_dev;
     gs.dt_dev = dt_dev;
     gs.counts = stored_counts(h);
+    gs.fold = h->d_fold;
     gs.K = K;
     gs.k0 = k0;
     gs.k1 = k1;
@@ -314,7 +318,8 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
       const unsigned* counts = stored_counts(h);
       for (const qaa::Pass& ps : passes)
         QAA_CK(timed(h, prof_kind(ps.kind), [&] {
-          return qaa::launch_planned_pass(lc, h->plan, ps, p, h->m, h->d_lp, ptab, btab, h->d_err, counts);
+          return qaa::launch_planned_pass(lc, h->plan, ps, p, h->m, h->d_lp, ptab, btab, h->d_err, counts,
+                                          h->d_fold);
         }));
     }
   }
@@ -341,7 +346,8 @@ int observe(qaa_ctx* h, const void* psi, double out[5]) {
     h->part_cap = need;
   }
   QAA_CK(timed(h, QAA_K_OBSERVE, [&] {
-    return qaa::launch_observables(lctx(h), static_cast<const float2*>(psi), h->n, h->m, h->d_lp, h->d_part, h->d_res);
+    return qaa::launch_observables(lctx(h), static_cast<const float2*>(psi), h->n, h->m, h->d_lp, h->d_part, h->d_res,
+                                   h->counts_state == 1 ? h->d_counts : nullptr, h->d_err);
   }));
   QAA_CK(cudaMemcpyAsync(h->h_res, h->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   QAA_CK(cudaStreamSynchronize(h->stream));
@@ -391,6 +397,7 @@ int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out) {
       cudaMalloc(&h->d_lp, mcap * sizeof(qaa::ClauseLP)) != cudaSuccess ||
       cudaMalloc(&h->d_res, 8 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_fold, qaa::kFoldBytes) != cudaSuccess ||
       cudaMallocHost(&h->h_res, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(QAA_E_NOMEM, "cannot allocate clause tables");
@@ -421,6 +428,7 @@ int qaa_destroy(qaa_handle h) {
   cudaFree(h->d_part);
   cudaFree(h->d_res);
   cudaFree(h->d_err);
+  cudaFree(h->d_fold);
   if (h->h_res) cudaFreeHost(h->h_res);
   for (auto& p : h->pending) {
     cudaEventDestroy(p.a);
@@ -469,6 +477,8 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   const bool same_form = (h->plan.wht_kind == qaa::kRotationForm) == (wht_kind == qaa::kRotationForm);
   h->plan.wht_kind = wht_kind;
   if (!same_form) qaa::set_default_run_c(h->plan);
+  // the tensor-core passes need the stored counts: look again if they were turned off
+  if ((wht_kind == 1 || wht_kind == 2) && h->counts_state == -1) h->counts_state = 0;
   // only the rotation form has a 12-bit low pass
   if (wht_kind != qaa::kRotationForm) qaa::narrow_low_pass(h->plan, q != 0 ? q : widest);
   return QAA_OK;

@@ -69,10 +69,11 @@ void build_passes(const PassPlan& plan, long long k0, long long k1, long long c0
 
 std::string describe_plan(const PassPlan& plan);
 
-// Launch one pass with the kernel family the plan selects.
+// Launch one pass with the kernel family the plan selects.  fold: kFoldBytes
+// of device scratch for the norm fold of the low passes (null: no fold).
 cudaError_t launch_planned_pass(const LaunchCtx& lc, const PassPlan& plan, const Pass& p, float2* psi, int m,
                                 const ClauseLP* cl, const float2* ptab, const float2* btab, int* err,
-                                const unsigned* counts = nullptr);
+                                const unsigned* counts = nullptr, double* fold = nullptr);
 
 constexpr long long kChunkSteps = 1024;
 
@@ -90,6 +91,7 @@ struct GraphSpec {
   const double* s_dev = nullptr;  // caller schedule on the device, or null for s_k = (k + 1/2)/K
   const double* dt_dev = nullptr;  // per-step lengths on the device, or null for the uniform dt
   const unsigned* counts = nullptr;  // stored per-tile clause counts (launch_lp_counts), or null
+  double* fold = nullptr;            // norm-fold slots (kFoldBytes), or null
   long long K = 0, k0 = 0, k1 = 0;
   int num_sms = 0;
   // graph scratch (graph_scratch_bytes): loop counter, kGraphUnroll + 1 P rows, kGraphUnroll B rows

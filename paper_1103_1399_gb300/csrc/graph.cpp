@@ -45,10 +45,21 @@ cudaError_t capture_into(cudaStream_t st, cudaGraph_t into, F&& body) {
 
 cudaError_t launch_all(const LaunchCtx& lc, const GraphSpec& s, const std::vector<Pass>& passes) {
   for (const Pass& p : passes) {
-    const cudaError_t e = launch_planned_pass(lc, *s.plan, p, s.psi, s.m, s.cl, s.prow, s.brow, s.err, s.counts);
+    const cudaError_t e =
+        launch_planned_pass(lc, *s.plan, p, s.psi, s.m, s.cl, s.prow, s.brow, s.err, s.counts, s.fold);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// The low passes of a captured piece end the range's steps first_rel,
+// first_rel + 1, ... (their norm-fold slots; build_passes numbers them from
+// the piece's own start).  A loop body's pieces start at multiples of
+// kGraphUnroll (even), so the slot parity is the same in every iteration.
+void number_low_passes(std::vector<Pass>& passes, long long first_rel) {
+  long long r = first_rel;
+  for (Pass& p : passes)
+    if (p.rel >= 0) p.rel = static_cast<int>(r++);
 }
 
 }  // namespace
@@ -129,6 +140,7 @@ cudaError_t build_evolve_graph(const GraphSpec& s, cudaGraphExec_t* out) {
       cudaError_t ec = rows(1, 1, kGraphUnroll, s.k0, kGraphUnroll, s.ctr);
       // kGraphUnroll merged steps: B rows 0.., P rows 1.. (build_passes' chunk convention)
       build_passes(plan, -1, 1ll << 40, 0, kGraphUnroll, passes);
+      number_low_passes(passes, 0);
       if (ec == cudaSuccess) ec = launch_all(lc, s, passes);
       if (ec == cudaSuccess) ec = launch_graph_advance(lc, s.ctr, kGraphUnroll, L * kGraphUnroll, h);
       return ec;
@@ -142,6 +154,7 @@ cudaError_t build_evolve_graph(const GraphSpec& s, cudaGraphExec_t* out) {
       const long long off = L * kGraphUnroll;
       cudaError_t ec = rows(1, 1 + off, static_cast<int>(R), s.k0 + off, static_cast<int>(R), nullptr);
       build_passes(plan, -1, 1ll << 40, 0, R, passes);
+      number_low_passes(passes, off);
       return ec == cudaSuccess ? launch_all(lc, s, passes) : ec;
     });
     if (e != cudaSuccess) return e;
@@ -151,6 +164,7 @@ cudaError_t build_evolve_graph(const GraphSpec& s, cudaGraphExec_t* out) {
   e = captured_child([&]() -> cudaError_t {
     cudaError_t ec = rows(1, s.k1 - s.k0, 1, s.k1 - 1, 1, nullptr);
     build_passes(plan, -1, 1, 0, 1, passes);  // one step, no first pass, ending in the last low pass
+    number_low_passes(passes, s.k1 - s.k0 - 1);
     return ec == cudaSuccess ? launch_all(lc, s, passes) : ec;
   });
   if (e != cudaSuccess) return e;

@@ -24,7 +24,7 @@
 
 namespace {
 
-constexpr size_t kResultBytes = 64;                                    // 5 doubles, padded
+constexpr size_t kResultBytes = 64;  // 5 doubles, then the bounded-wait error word at byte 48
 constexpr size_t kPartialBytes = static_cast<size_t>(QAA_NOALLOC_MAX_PARTIALS) * sizeof(double);
 constexpr size_t kClauseBytes = static_cast<size_t>(QAA_MAX_CLAUSES) * sizeof(qaa::ClauseLP);
 constexpr size_t kScratchBytes = kResultBytes + kPartialBytes + kClauseBytes;
@@ -125,14 +125,21 @@ extern "C" int qaa_observables_noalloc(int n, const int32_t* clauses, int m, con
     if (err != cudaSuccess) return noalloc_fail(QAA_E_CUDA, std::string("clause upload: ") + cudaGetErrorString(err));
   }
   // Every partial slot and result the kernels read is written earlier in the
-  // same call, so nothing left by a previous call needs clearing.
+  // same call; only the error word must start at zero.
+  int* d_errword = reinterpret_cast<int*>(base + 48);
+  cudaError_t err = cudaMemsetAsync(d_errword, 0, sizeof(int), stream);
+  if (err != cudaSuccess) return noalloc_fail(QAA_E_CUDA, std::string("error word: ") + cudaGetErrorString(err));
   const qaa::LaunchCtx lc{stream, num_sms};
-  cudaError_t err = qaa::launch_observables(lc, static_cast<const float2*>(psi), n, m, d_clauses, d_partials, d_result);
+  err = qaa::launch_observables(lc, static_cast<const float2*>(psi), n, m, d_clauses, d_partials, d_result, nullptr,
+                                d_errword);
   if (err != cudaSuccess) return noalloc_fail(QAA_E_CUDA, std::string("observables: ") + cudaGetErrorString(err));
-  double r[5];
+  double r[8];
   err = cudaMemcpyAsync(r, d_result, sizeof(r), cudaMemcpyDeviceToHost, stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
   if (err != cudaSuccess) return noalloc_fail(QAA_E_CUDA, std::string("result read-back: ") + cudaGetErrorString(err));
+  int werr = 0;
+  std::memcpy(&werr, reinterpret_cast<const unsigned char*>(r) + 48, sizeof(int));
+  if (werr != 0) return noalloc_fail(QAA_E_TIMEOUT, "a bounded wait on a TMA copy expired in a correlation pass");
   out->norm = r[0];
   out->expect_hp = r[1];
   out->ground_prob = r[2];

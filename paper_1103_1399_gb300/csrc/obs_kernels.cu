@@ -5,25 +5,44 @@
 //   norm = sum |psi|^2, <H_P> = sum E |psi|^2, ground = sum_{E=0} |psi|^2,
 //   count of E = 0, and C = sum_i sum_{x: bit i-1 clear} Re(conj psi_x psi_(x+2^(i-1)))
 //   from which <H_B> = n/2 norm - C.
-// norm, <H_P> and the ground probability: every product formed in FP64 from
-// the FP32 amplitudes (exact) and summed in FP64.  The pair correlations C
-// (n pair products per amplitude, the bulk of the arithmetic) are formed and
-// summed in FP32 over one thread's share of one tile or column (at most 320
-// products) and accumulated in FP64 beyond that: GB300's FP64 rate is a small
-// fraction of its FP32 rate, and with FP64 pair products the reductions ran at
-// ~2% of the HBM bound.  The FP32 stage adds at most ~320 ulp of the largest
-// product to each partial; independent partials average out in the FP64 sum.
-// Every sum runs in a fixed order (per thread, a fixed shuffle/shared-memory
-// tree per block, the partials by one block): bit-identical run to run.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so no per-amplitude
+// work is done in FP64 here.  norm, <H_P> and the ground probability are formed
+// exactly in FP32 pieces and summed as double-floats (an FP32 value plus its
+// exact rounding error):
+//   * |psi|^2 = re^2 + im^2: each square split into its FP32 product and the
+//     product's exact error (one FMA), the two products added with Knuth's
+//     TwoSum (exact result as sum + error);
+//   * E |psi|^2: the same split of E times the FP32 part;
+//   * each lane's running sums over its 32 amplitudes of a tile: TwoSum into a
+//     (sum, error) pair, on packed f32x2 instructions for (norm, <H_P>);
+//   * once per tile the pairs are added into the lane's FP64 totals.
+// The result agrees with exact-product FP64 sums to about 1e-14 relative.
+// The pair correlations C (n pair products per amplitude) are formed and
+// summed in FP32 over one thread's share of one tile (at most 320 products)
+// and accumulated in FP64 beyond that.  Every sum runs in a fixed order (per
+// thread, a fixed shuffle/shared-memory tree per block, the partials by one
+// block): bit-identical run to run.
+//
+// Passes over the state: the low kernel reads it once (bits 0..9 of the index
+// in one warp's 1024-amplitude tile: the norm-type sums and the pair
+// correlations of bits 0..9), and bits 10..n-1 are covered in groups of at
+// most 10 bits by read-only strided-tile passes (corr_tma_kernel in
+// tma_kernels.cu; plain loads in groups of 5 when TMA is unavailable): 3 reads
+// of the state at n = 30.
 #include "device_common.cuh"
 
 namespace qaa {
 
 constexpr int kObsWarps = 8;
 constexpr int kObsQuant = 5;  // norm, hp, ground, count, corr(low bits)
+constexpr int kObsRow = 33;   // padded transpose rows (as the low passes)
 
-static size_t obs_low_smem(int m) {
-  return 16u * static_cast<size_t>(m) + static_cast<size_t>(kObsWarps) * 8u * static_cast<size_t>(m + 16) + 64u * 8u;
+static size_t obs_low_smem(int m, bool stored) {
+  const size_t tile = static_cast<size_t>(kObsWarps) * 8u * kObsRow * 32u;
+  if (stored) return tile + 64u * 8u;
+  return 16u * static_cast<size_t>(m) + tile + static_cast<size_t>(kObsWarps) * 8u * static_cast<size_t>(m + 16) +
+         64u * 8u;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -71,76 +90,156 @@ __global__ void __launch_bounds__(kObsWarps * 32)
   }
 }
 
+// ---- double-float accumulation ------------------------------------------------
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// One lane's sums over a tile: (norm, <H_P>) as packed (sum, error) pairs, the
+// ground probability as a scalar pair, the ground count.
+struct ObsAcc {
+  unsigned long long s = 0ull, e = 0ull;
+  float gs = 0.f, ge = 0.f, gc = 0.f;
+};
+
+// Knuth's TwoSum: s + b = s' + err exactly; err added to e.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float b) {
+  const float t = s + b;
+  const float bb = t - s;
+  e += (s - (t - bb)) + (b - bb);
+  s = t;
+}
+
+// Add |v|^2 (and E |v|^2, and |v|^2 to the ground sums when `ground`).
+__device__ __forceinline__ void obs_add(ObsAcc& a, float2 v, float E, bool ground) {
+  const unsigned long long vv = f2_bits(v);
+  unsigned long long h;
+  asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(h) : "l"(vv));
+  const unsigned long long l = f2fma(vv, vv, h ^ 0x8000000080000000ull);  // exact errors of re^2, im^2
+  const float2 hf = bits_f2(h), lf = bits_f2(l);
+  // p = re^2 + im^2 = ph + pl (pl: TwoSum error of the two squares plus their errors)
+  const float ph = hf.x + hf.y;
+  const float bb = ph - hf.x;
+  const float pl = ((hf.x - (ph - bb)) + (hf.y - bb)) + (lf.x + lf.y);
+  const float eh = E * ph;
+  const float el = fmaf(E, pl, fmaf(E, ph, -eh));  // E ph - eh exactly, plus E pl
+  const unsigned long long t = f2_bits(make_float2(ph, eh));
+  const unsigned long long s = f2add(a.s, t);
+  const unsigned long long b2 = f2sub(s, a.s);
+  const unsigned long long err = f2add(f2sub(a.s, f2sub(s, b2)), f2sub(t, b2));
+  a.s = s;
+  a.e = f2add(a.e, f2add(err, f2_bits(make_float2(pl, el))));
+  if (ground) {
+    two_sum_acc(a.gs, a.ge, ph);
+    a.ge += pl;
+    a.gc += 1.f;
+  }
+}
+
+template <int R>
+struct ObsAddUnroll {
+  __device__ __forceinline__ static void run(ObsAcc& a, const float2 (&v)[32], const unsigned (&pl)[kPlanes],
+                                             int nconst, int lane, int N) {
+    const unsigned w = extract_pair<R>(pl);
+    const int e0 = nconst + static_cast<int>(w & 0xffffu), e1 = nconst + static_cast<int>(w >> 16);
+    // layout Y: register r holds index bits 0..4, the lane bits 5..9
+    obs_add(a, v[R], static_cast<float>(e0), e0 == 0 && R + 32 * lane < N);
+    obs_add(a, v[R + 16], static_cast<float>(e1), e1 == 0 && R + 16 + 32 * lane < N);
+    ObsAddUnroll<R + 1>::run(a, v, pl, nconst, lane, N);
+  }
+};
+template <>
+struct ObsAddUnroll<16> {
+  __device__ __forceinline__ static void run(ObsAcc&, const float2 (&)[32], const unsigned (&)[kPlanes], int, int,
+                                             int) {}
+};
+
+// Pair products over register bits [0, 5) with index bit (b + shift) < n.
+__device__ __forceinline__ unsigned long long reg_pairs(const float2 (&v)[32], int shift, int n,
+                                                        unsigned long long c) {
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if (b + shift < n) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (!(r & (1 << b))) c = f2fma(f2_bits(v[r]), f2_bits(v[r | (1 << b)]), c);
+    }
+  }
+  return c;
+}
+
+// Low kernel: one 1024-amplitude tile per warp.  Loaded in layout X (lane =
+// bits 0..4, register = bits 5..9): the pairs of bits 5..9; transposed to
+// layout Y (register = bits 0..4, lane = bits 5..9): the pairs of bits 0..4
+// and the norm-type sums with the energies of layout Y, read from the stored
+// per-tile counts (STORED) or folded and counted from the clauses.  n < 10:
+// one tile, amplitudes beyond 2^n read as zero and excluded from the count.
+template <bool STORED>
 __global__ void __launch_bounds__(kObsWarps * 32)
-    obs_low_kernel(const float2* __restrict__ psi, int n, int m, const ClauseLP* __restrict__ cl, long long ntiles,
-                   double* __restrict__ partials) {
+    obs_low_kernel(const float2* __restrict__ psi, int n, int m, const ClauseLP* __restrict__ cl,
+                   const unsigned* __restrict__ counts, long long ntiles, double* __restrict__ partials) {
   extern __shared__ __align__(16) unsigned char smem[];
-  ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint2* s_act = reinterpret_cast<uint2*>(smem + 16u * m) + warp * (m + 16);
-  double* s_red = reinterpret_cast<double*>(smem + 16u * m + static_cast<size_t>(kObsWarps) * 8u * (m + 16));
-  for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
+  const size_t cl_bytes = STORED ? 0u : 16u * static_cast<size_t>(m);
+  ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
+  float2* s_tile = reinterpret_cast<float2*>(smem + cl_bytes) + warp * (kObsRow * 32);
+  unsigned char* after_tiles = smem + cl_bytes + static_cast<size_t>(kObsWarps) * 8u * kObsRow * 32u;
+  uint2* s_act = reinterpret_cast<uint2*>(after_tiles) + warp * (m + 16);
+  double* s_red = reinterpret_cast<double*>(after_tiles + (STORED ? 0u : static_cast<size_t>(kObsWarps) * 8u * (m + 16)));
+  if (!STORED) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
+  }
   __syncthreads();
-  const unsigned long long N = 1ull << n;
-  double a_norm = 0.0, a_hp = 0.0, a_gp = 0.0, a_gc = 0.0, a_corr = 0.0;
+  const int N = n < kLowBits ? (1 << n) : (1 << kLowBits);  // amplitudes per tile that exist
+  double d_norm = 0.0, d_hp = 0.0, d_gp = 0.0, d_gc = 0.0, d_corr = 0.0;
   for (long long tile = static_cast<long long>(blockIdx.x) * kObsWarps + warp; tile < ntiles;
        tile += static_cast<long long>(gridDim.x) * kObsWarps) {
-    const unsigned long long base = static_cast<unsigned long long>(tile) << kLowBits;
+    const float2* g = psi + (static_cast<unsigned long long>(tile) << kLowBits);
     float2 v[32];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const unsigned long long x = base + lane + 32 * r;
-      v[r] = x < N ? psi[x] : make_float2(0.0f, 0.0f);
-    }
-    int nconst, npad;
+    for (int r = 0; r < 32; ++r) v[r] = lane + 32 * r < N ? g[lane + 32 * r] : make_float2(0.0f, 0.0f);
+    unsigned long long c2 = reg_pairs(v, 5, n, 0ull);  // index bits 5..9
+    // layout X -> Y through the padded tile
     __syncwarp();
-    fold_tile<false>(s_cl, m, static_cast<unsigned>(tile), lane, s_act, nconst, npad);
-    int e[32];
-    energies(e, s_act, npad, nconst, 1u << lane);
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const double re = v[r].x, im = v[r].y;
-      const double p = fma(re, re, im * im);
-      a_norm += p;
-      a_hp = fma(static_cast<double>(e[r]), p, a_hp);
-      const bool valid = base + lane + 32 * r < N;
-      if (e[r] == 0 && valid) {
-        a_gp += p;
-        a_gc += 1.0;
-      }
+    for (int r = 0; r < 32; ++r) s_tile[lane + kObsRow * r] = v[r];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = s_tile[kObsRow * lane + r];
+    c2 = reg_pairs(v, 0, n, c2);  // index bits 0..4
+    unsigned pl[kPlanes];
+    int nconst;
+    if (STORED) {
+      load_counts(counts, tile, lane, pl, nconst);
+    } else {
+      int npad;
+      fold_tile<true>(s_cl, m, static_cast<unsigned>(tile), lane, s_act, nconst, npad);
+      count_active(s_act, npad, 1u << lane, pl);
     }
-    float f_corr = 0.f;
-    // pairs across register bits (index bits 5..9)
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      if (5 + b < n) {
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          if (!(r & (1 << b))) {
-            const float2 u = v[r], w = v[r | (1 << b)];
-            f_corr = fmaf(u.x, w.x, f_corr);
-            f_corr = fmaf(u.y, w.y, f_corr);
-          }
-        }
-      }
+    ObsAcc a;
+    ObsAddUnroll<0>::run(a, v, pl, nconst, lane, N);
+    const float2 s = bits_f2(a.s), e = bits_f2(a.e), c = bits_f2(c2);
+    d_norm += static_cast<double>(s.x) + static_cast<double>(e.x);
+    d_hp += static_cast<double>(s.y) + static_cast<double>(e.y);
+    if (a.gc != 0.f) {
+      d_gp += static_cast<double>(a.gs) + static_cast<double>(a.ge);
+      d_gc += static_cast<double>(a.gc);
     }
-    // pairs across lanes (index bits 0..4)
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      if (b < n) {
-        const float keep = (lane & (1 << b)) ? 0.f : 1.f;  // count each pair once
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          const float wx = __shfl_xor_sync(0xffffffffu, v[r].x, 1 << b);
-          const float wy = __shfl_xor_sync(0xffffffffu, v[r].y, 1 << b);
-          f_corr = fmaf(keep * v[r].x, wx, f_corr);
-          f_corr = fmaf(keep * v[r].y, wy, f_corr);
-        }
-      }
-    }
-    a_corr += static_cast<double>(f_corr);
+    d_corr += static_cast<double>(c.x + c.y);
   }
-  const double q[kObsQuant] = {a_norm, a_hp, a_gp, a_gc, a_corr};
+  const double q[kObsQuant] = {d_norm, d_hp, d_gp, d_gc, d_corr};
 #pragma unroll
   for (int k = 0; k < kObsQuant; ++k) {
     const double t = block_sum(q[k], s_red);
@@ -148,8 +247,9 @@ __global__ void __launch_bounds__(kObsWarps * 32)
   }
 }
 
-// Pair correlations for index bits [a, a+w) (a >= 10, w <= 5): one thread per
-// column (the other index bits), coalesced over the low bits.
+// Pair correlations for index bits [a, a+w) (a >= 10, w <= 5) with plain
+// loads: one thread per column (the other index bits), coalesced over the low
+// bits.  Used for n = 11..14 and when TMA is unavailable.
 __global__ void __launch_bounds__(256)
     corr_kernel(const float2* __restrict__ psi, int a, int w, long long ncols, double* __restrict__ partials) {
   __shared__ double s_red[32];
@@ -206,10 +306,33 @@ __global__ void __launch_bounds__(256)
 
 static int obs_grid(int num_sms) { return 2 * num_sms; }
 
-static int corr_kernels(int n) { return n > kLowBits ? (n - kLowBits + 4) / 5 : 0; }
+// Correlation passes over bits [10, n): contiguous groups of 5..10 bits (as
+// even as possible) on the TMA tile passes, else groups of at most 5 bits with
+// plain loads (and always for n - 10 < 5).
+struct CorrPlan {
+  int ng = 0;
+  int a[8] = {}, q[8] = {};
+  bool tma = false;
+};
+static CorrPlan corr_plan(int n, bool allow_tma) {
+  CorrPlan p;
+  const int rest = n - kLowBits;
+  if (rest <= 0) return p;
+  p.tma = allow_tma && rest >= 5 && tma_available();
+  const int widest = p.tma ? 10 : 5;
+  p.ng = (rest + widest - 1) / widest;
+  int a = kLowBits;
+  for (int g = 0; g < p.ng; ++g) {
+    p.q[g] = rest / p.ng + (g < rest % p.ng ? 1 : 0);
+    p.a[g] = a;
+    a += p.q[g];
+  }
+  return p;
+}
 
+// Room for either plan (the plain-load one has more groups).
 size_t obs_partials_len(int n, int num_sms) {
-  return static_cast<size_t>(kObsQuant + corr_kernels(n)) * obs_grid(num_sms);
+  return static_cast<size_t>(kObsQuant + corr_plan(n, false).ng) * obs_grid(num_sms);
 }
 
 cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, const ClauseLP* cl) {
@@ -224,23 +347,29 @@ cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, con
 }
 
 cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, int m, const ClauseLP* cl,
-                               double* partials, double* result) {
+                               double* partials, double* result, const unsigned* counts, int* err_word) {
   const int P = obs_grid(lc.num_sms);
   const long long ntiles = n > kLowBits ? (1ll << (n - kLowBits)) : 1ll;
-  const size_t smem = obs_low_smem(m);
-  cudaError_t err = allow_smem(reinterpret_cast<const void*>(obs_low_kernel), obs_low_smem(QAA_MAX_CLAUSES_DEV));
+  const bool stored = counts != nullptr && n > kLowBits;
+  auto kern = stored ? obs_low_kernel<true> : obs_low_kernel<false>;
+  cudaError_t err = allow_smem(reinterpret_cast<const void*>(kern), obs_low_smem(QAA_MAX_CLAUSES_DEV, stored));
   if (err != cudaSuccess) return err;
-  obs_low_kernel<<<P, kObsWarps * 32, smem, lc.stream>>>(psi, n, m, cl, ntiles, partials);
+  kern<<<P, kObsWarps * 32, obs_low_smem(m, stored), lc.stream>>>(psi, n, m, cl, counts, ntiles, partials);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  const int nc = corr_kernels(n);
-  for (int k = 0; k < nc; ++k) {
-    const int a = kLowBits + 5 * k;
-    const int w = (n - a) < 5 ? (n - a) : 5;
-    const long long ncols = 1ll << (n - w);
-    corr_kernel<<<P, 256, 0, lc.stream>>>(psi, a, w, ncols, partials + static_cast<size_t>(kObsQuant + k) * P);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  // the TMA passes need an error word for their bounded waits
+  const CorrPlan cp = corr_plan(n, err_word != nullptr && reinterpret_cast<uintptr_t>(psi) % 16u == 0);
+  for (int k = 0; k < cp.ng; ++k) {
+    double* part = partials + static_cast<size_t>(kObsQuant + k) * P;
+    if (cp.tma) {
+      err = launch_corr_tma(lc, psi, n, cp.a[k], cp.q[k], part, P, err_word);
+    } else {
+      const long long ncols = 1ll << (n - cp.q[k]);
+      corr_kernel<<<P, 256, 0, lc.stream>>>(psi, cp.a[k], cp.q[k], ncols, part);
+      err = cudaGetLastError();
+    }
+    if (err != cudaSuccess) return err;
   }
-  obs_reduce_kernel<<<1, 256, 0, lc.stream>>>(partials, P, kObsQuant + nc, result);
+  obs_reduce_kernel<<<1, 256, 0, lc.stream>>>(partials, P, kObsQuant + cp.ng, result);
   return cudaGetLastError();
 }
 

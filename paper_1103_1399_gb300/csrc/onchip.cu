@@ -22,7 +22,7 @@ constexpr int kOnchipThreads = 512;
 // columns along any 5-bit group, base + immediate addressing within a column).
 __device__ __forceinline__ int oswz(int x) { return x + (x >> 5); }
 
-enum : unsigned { kPreP = 1u, kW1 = 2u, kMidB = 4u, kW2 = 8u, kPostP = 16u, kW3 = 32u };
+enum : unsigned { kPreP = 1u, kW1 = 2u, kMidB = 4u, kW2 = 8u, kPostP = 16u, kW3 = 32u, kNorm = 64u };
 
 template <int W>
 __device__ __forceinline__ void col_wht(float2 (&v)[1 << W]) {
@@ -35,10 +35,13 @@ __device__ __forceinline__ void col_wht(float2 (&v)[1 << W]) {
   }
 }
 
+// kNorm: add |psi|^2 of the round's outputs to *nacc (FP32: at most one column
+// per thread at n <= 14); cs scales the popcount phase (the norm fold of the
+// previous step).
 template <int W>
 __device__ void onchip_round(float2* __restrict__ s_psi, const uint16_t* __restrict__ s_e, int n, int b0,
                              unsigned flags, const float2* __restrict__ prow_a, const float2* __restrict__ brow,
-                             const float2* __restrict__ prow_b) {
+                             const float2* __restrict__ prow_b, float cs, float* nacc) {
   const int ncols = (1 << n) >> W;
   const int lo_mask = (1 << b0) - 1;
   for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
@@ -59,6 +62,10 @@ __device__ void onchip_round(float2* __restrict__ s_psi, const uint16_t* __restr
       const int pc = __popc(xb);
 #pragma unroll
       for (int r = 0; r < (1 << W); ++r) v[r] = cmul(v[r], brow[pc + __popc(r)]);
+      if (cs != 1.0f) {
+#pragma unroll
+        for (int r = 0; r < (1 << W); ++r) v[r] = make_float2(v[r].x * cs, v[r].y * cs);
+      }
     }
     if (flags & kW2) col_wht<W>(v);
     if (flags & kPostP) {
@@ -68,21 +75,65 @@ __device__ void onchip_round(float2* __restrict__ s_psi, const uint16_t* __restr
     if (flags & kW3) col_wht<W>(v);
 #pragma unroll
     for (int r = 0; r < (1 << W); ++r) s_psi[sx + r * rstep] = v[r];
+    if (flags & kNorm) {
+      // pairwise tree over the column (at most 5 levels of FP32 rounding)
+      float p[1 << W];
+#pragma unroll
+      for (int r = 0; r < (1 << W); ++r) p[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+#pragma unroll
+      for (int h = (1 << W) >> 1; h > 0; h >>= 1) {
+#pragma unroll
+        for (int r = 0; r < h; ++r) p[r] += p[r + h];
+      }
+      *nacc += p[0];
+    }
   }
 }
 
 __device__ __forceinline__ void round_dispatch(float2* s_psi, const uint16_t* s_e, int n, int g, unsigned flags,
-                                               const float2* pa, const float2* br, const float2* pb) {
+                                               const float2* pa, const float2* br, const float2* pb, float cs,
+                                               float* nacc) {
   const int b0 = 5 * g;
   const int w = (n - b0) < 5 ? (n - b0) : 5;
   switch (w) {
-    case 1: onchip_round<1>(s_psi, s_e, n, b0, flags, pa, br, pb); break;
-    case 2: onchip_round<2>(s_psi, s_e, n, b0, flags, pa, br, pb); break;
-    case 3: onchip_round<3>(s_psi, s_e, n, b0, flags, pa, br, pb); break;
-    case 4: onchip_round<4>(s_psi, s_e, n, b0, flags, pa, br, pb); break;
-    default: onchip_round<5>(s_psi, s_e, n, b0, flags, pa, br, pb); break;
+    case 1: onchip_round<1>(s_psi, s_e, n, b0, flags, pa, br, pb, cs, nacc); break;
+    case 2: onchip_round<2>(s_psi, s_e, n, b0, flags, pa, br, pb, cs, nacc); break;
+    case 3: onchip_round<3>(s_psi, s_e, n, b0, flags, pa, br, pb, cs, nacc); break;
+    case 4: onchip_round<4>(s_psi, s_e, n, b0, flags, pa, br, pb, cs, nacc); break;
+    default: onchip_round<5>(s_psi, s_e, n, b0, flags, pa, br, pb, cs, nacc); break;
   }
   __syncthreads();
+}
+
+// The norm fold of a step (as in the streaming low passes): the block's sum of
+// one FP32 value per thread -- a fixed FP32 shuffle tree per warp, the warps'
+// sums added in FP64 by thread 0 -- and, with ref > 0, the factor that brings
+// it back to ref times the power of two nearest to sum / ref; without ref the
+// sum itself.  Thread 0 alone does the FP64 work (GB300's FP64 rate is a small
+// fraction of its FP32 rate) and every thread gets the result.
+__device__ double onchip_fold(float v, double ref) {
+  __shared__ float s_w[kOnchipThreads / 32];
+  __shared__ double s_out;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) s_w[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += static_cast<double>(s_w[w]);
+    double out = t;
+    if (ref > 0.0) {
+      out = 1.0;
+      if (t > 0.0 && isfinite(t) && isfinite(ref)) {
+        const double q = ref / t;
+        out = sqrt(ldexp(q, static_cast<int>(rint(-log2(q)))));
+      }
+    }
+    s_out = out;
+  }
+  __syncthreads();
+  return s_out;
 }
 
 // Shared layout: [psi slots | E slots (uint16) | clauses], every region starting
@@ -113,8 +164,13 @@ __device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseM
   // the uniform start state 2^(-n/2) (Sec. 2.1, value rounded on the host as
   // for qaa_init_uniform), or the caller's state
   const float2 u = make_float2(init_val, 0.0f);
-  for (int x = threadIdx.x; x < N; x += blockDim.x) s_psi[oswz(x)] = init_uniform ? u : psi[x];
-  __syncthreads();
+  float racc = 0.0f;  // |psi|^2 of the input: the norm every step is folded back to
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const float2 a = init_uniform ? u : psi[x];
+    s_psi[oswz(x)] = a;
+    racc += fmaf(a.x, a.x, a.y * a.y);  // at most 32 terms per thread (N <= 2^14)
+  }
+  const double nref = onchip_fold(racc, 0.0);
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     int e = 0;
     for (int c = 0; c < m; ++c) {
@@ -128,22 +184,26 @@ __device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseM
   const int G = (n + 4) / 5;
   const int mp1 = m + 1;
   bool w0_done = false;
+  float cs = 1.0f;  // norm fold of the previous step, applied with the popcount phase
   for (int j = 0; j < nsteps; ++j) {
     const float2* p_first = ptab;  // row 0, only when first_p and j == 0
     const float2* p_next = ptab + static_cast<size_t>(j + 1) * mp1;
     const float2* brow = btab + static_cast<size_t>(j) * (n + 1);
     const bool last = j == nsteps - 1;
     const unsigned pre = (j == 0 && first_p) ? kPreP : 0u;
+    const unsigned nrm = last ? 0u : kNorm;
+    float nacc = 0.0f;
     if (G == 1) {
-      const unsigned f = pre | (w0_done ? 0u : kW1) | kMidB | kW2 | kPostP | (last ? 0u : kW3);
-      round_dispatch(s_psi, s_e, n, 0, f, p_first, brow, p_next);
+      const unsigned f = pre | (w0_done ? 0u : kW1) | kMidB | kW2 | kPostP | (last ? 0u : kW3) | nrm;
+      round_dispatch(s_psi, s_e, n, 0, f, p_first, brow, p_next, cs, &nacc);
     } else {
-      if (!w0_done) round_dispatch(s_psi, s_e, n, 0, pre | kW1, p_first, brow, p_next);
-      for (int g = 1; g <= G - 2; ++g) round_dispatch(s_psi, s_e, n, g, kW1, p_first, brow, p_next);
-      round_dispatch(s_psi, s_e, n, G - 1, kW1 | kMidB | kW2, p_first, brow, p_next);
-      for (int g = G - 2; g >= 1; --g) round_dispatch(s_psi, s_e, n, g, kW1, p_first, brow, p_next);
-      round_dispatch(s_psi, s_e, n, 0, kW1 | kPostP | (last ? 0u : kW3), p_first, brow, p_next);
+      if (!w0_done) round_dispatch(s_psi, s_e, n, 0, pre | kW1, p_first, brow, p_next, cs, &nacc);
+      for (int g = 1; g <= G - 2; ++g) round_dispatch(s_psi, s_e, n, g, kW1, p_first, brow, p_next, cs, &nacc);
+      round_dispatch(s_psi, s_e, n, G - 1, kW1 | kMidB | kW2, p_first, brow, p_next, cs, &nacc);
+      for (int g = G - 2; g >= 1; --g) round_dispatch(s_psi, s_e, n, g, kW1, p_first, brow, p_next, cs, &nacc);
+      round_dispatch(s_psi, s_e, n, 0, kW1 | kPostP | (last ? 0u : kW3) | nrm, p_first, brow, p_next, cs, &nacc);
     }
+    if (!last) cs = static_cast<float>(onchip_fold(nacc, nref > 0.0 ? nref : -1.0));
     w0_done = !last;
   }
   for (int x = threadIdx.x; x < N; x += blockDim.x) psi[x] = s_psi[oswz(x)];

@@ -59,7 +59,7 @@ __host__ __device__ inline size_t lp_smem_bytes(int m) {
 template <int KIND>
 __global__ void __launch_bounds__(kLpWarps * 32, 2)
     lp_kernel(float2* __restrict__ psi, int m, const ClauseLP* __restrict__ cl,
-              const float2* __restrict__ prow, long long ntiles) {
+              const float2* __restrict__ prow, long long ntiles, const NormFold nf) {
   extern __shared__ __align__(16) unsigned char smem[];
   ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
   float2* s_pt = reinterpret_cast<float2*>(smem + 16 * m);
@@ -69,9 +69,12 @@ __global__ void __launch_bounds__(kLpWarps * 32, 2)
   uint2* s_act = reinterpret_cast<uint2*>(smem + off + 8u * kLpTileSlots * kLpWarps) + warp * (m + 16);
 
   for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
-  for (int i = threadIdx.x; i <= m; i += blockDim.x) s_pt[i] = prow[i];
+  const double fc = fold_factor_block(nf);  // norm correction of the previous step (1 if none)
+  for (int i = threadIdx.x; i <= m; i += blockDim.x)
+    s_pt[i] = make_float2(static_cast<float>(prow[i].x * fc), static_cast<float>(prow[i].y * fc));
   __syncthreads();
 
+  double nacc = 0.0;
   const long long step = static_cast<long long>(gridDim.x) * kLpWarps;
   for (long long tile = static_cast<long long>(blockIdx.x) * kLpWarps + warp; tile < ntiles; tile += step) {
     float2* g = psi + (tile << kLowBits);
@@ -105,7 +108,9 @@ __global__ void __launch_bounds__(kLpWarps * 32, 2)
     }
 #pragma unroll
     for (int r = 0; r < 32; ++r) g[lane + 32 * r] = v[r];
+    if (nf.out) nacc += static_cast<double>(tile_norm(v));
   }
+  fold_store(nf, nacc);
 }
 
 // ---------------------------------------------------------------------------
@@ -348,7 +353,8 @@ static cudaError_t launch_sp(const LaunchCtx& lc, float2* psi, int n, int a, boo
 }
 
 template <int KIND>
-static cudaError_t launch_lp(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl, const float2* prow) {
+static cudaError_t launch_lp(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl, const float2* prow,
+                            const NormFold& nf) {
   const long long ntiles = 1ll << (n - kLowBits);
   const size_t smem = lp_smem_bytes(m);
   auto kern = lp_kernel<KIND>;
@@ -361,16 +367,17 @@ static cudaError_t launch_lp(const LaunchCtx& lc, float2* psi, int n, int m, con
   long long grid = static_cast<long long>(occ) * lc.num_sms;
   const long long need = (ntiles + kLpWarps - 1) / kLpWarps;
   if (grid > need) grid = need;
-  kern<<<static_cast<unsigned>(grid), kLpWarps * 32, smem, lc.stream>>>(psi, m, cl, prow, ntiles);
+  if (grid > kFoldSlot - 1) grid = kFoldSlot - 1;  // one norm-fold partial per CTA
+  kern<<<static_cast<unsigned>(grid), kLpWarps * 32, smem, lc.stream>>>(psi, m, cl, prow, ntiles, nf);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pass(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
-                        const float2* ptab, const float2* btab) {
+                        const float2* ptab, const float2* btab, const NormFold& nf) {
   switch (p.kind) {
-    case kLpFirst: return launch_lp<kLpFirst>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1));
-    case kLpMerge: return launch_lp<kLpMerge>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1));
-    case kLpLast: return launch_lp<kLpLast>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1));
+    case kLpFirst: return launch_lp<kLpFirst>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), nf);
+    case kLpMerge: return launch_lp<kLpMerge>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), nf);
+    case kLpLast: return launch_lp<kLpLast>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1), nf);
     case kSpW:
     case kSpWBW: {
       const bool wbw = p.kind == kSpWBW;

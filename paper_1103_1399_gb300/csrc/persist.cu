@@ -29,6 +29,7 @@ struct PersistArgs {
   const float2* btab;  // K rows of n + 1 entries
   unsigned* bar;       // [0] arrivals, [1] generation; zeroed before launch
   int* err;
+  double* fold;        // norm-fold slots (kFoldBytes), or null
   int n, m, K;
   int ng, phase_group;
   int ga[3], gq[3];  // contiguous strided groups [ga, ga + gq)
@@ -81,11 +82,20 @@ __device__ __forceinline__ void y2x(float2 (&v)[32], float2* __restrict__ s, int
   __syncwarp();
 }
 
+// rel: the step this low pass ends (-1 for the first pass), selecting the
+// norm-fold slots as for the streaming passes; the correction of the previous
+// step is applied as a factor after the P phase (the P row stays in global
+// memory here).
 template <int KIND>
 __device__ void low_pass(const PersistArgs& A, const ClauseLP* s_cl, float2* s_tile, uint2* s_act,
-                         const float2* __restrict__ tab) {
+                         const float2* __restrict__ tab, int rel) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ntiles = 1ll << (A.n - kLowBits);
+  Pass fp{};
+  fp.rel = rel;
+  const NormFold nf = fold_for(A.fold, fp);
+  const float fc = static_cast<float>(fold_factor_block(nf));
+  double nacc = 0.0;
   for (long long tile = static_cast<long long>(blockIdx.x) * kPersistWarps + warp; tile < ntiles;
        tile += static_cast<long long>(gridDim.x) * kPersistWarps) {
     float2* g = A.psi + (tile << kLowBits);
@@ -108,13 +118,19 @@ __device__ void low_pass(const PersistArgs& A, const ClauseLP* s_cl, float2* s_t
       x2y(v, s_tile, lane);
       reg_wht<0, 5>(v);
       apply_p_phase(v, pl, nconst, tab);
+      if (fc != 1.0f) {
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = make_float2(v[r].x * fc, v[r].y * fc);
+      }
       if (KIND == kLpMerge) reg_wht<0, 5>(v);
       y2x(v, s_tile, lane);
       if (KIND == kLpMerge) reg_wht<0, 5>(v);
     }
 #pragma unroll
     for (int r = 0; r < 32; ++r) g[lane + 32 * r] = v[r];
+    if (nf.out) nacc += static_cast<double>(tile_norm(v));
   }
+  fold_store(nf, nacc);
 }
 
 // -------------------------------------------------------- strided pass ------
@@ -223,7 +239,7 @@ __global__ void __launch_bounds__(kPersistThreads) persist_kernel(PersistArgs A)
   const int pg = A.phase_group;
   auto sync = [&]() { return grid_barrier(A.bar, A.err); };
   // first pass of the run: P(row 0) then W over bits 0..9, then the other groups up
-  low_pass<kLpFirst>(A, s_cl, s_wtile, s_act, A.ptab);
+  low_pass<kLpFirst>(A, s_cl, s_wtile, s_act, A.ptab, -1);
   if (!sync()) return;
   for (int g = 0; g < A.ng; ++g) {
     if (g == pg) continue;
@@ -240,10 +256,10 @@ __global__ void __launch_bounds__(kPersistThreads) persist_kernel(PersistArgs A)
     }
     const float2* prow = A.ptab + static_cast<size_t>(k + 1) * mp1;
     if (k == A.K - 1) {
-      low_pass<kLpLast>(A, s_cl, s_wtile, s_act, prow);
+      low_pass<kLpLast>(A, s_cl, s_wtile, s_act, prow, k);
       break;  // the kernel's end orders the final pass before any later work
     }
-    low_pass<kLpMerge>(A, s_cl, s_wtile, s_act, prow);
+    low_pass<kLpMerge>(A, s_cl, s_wtile, s_act, prow, k);
     if (!sync()) return;
     for (int g = 0; g < A.ng; ++g) {
       if (g == pg) continue;
@@ -254,8 +270,10 @@ __global__ void __launch_bounds__(kPersistThreads) persist_kernel(PersistArgs A)
 }
 
 cudaError_t launch_persist(const LaunchCtx& lc, const PersistPlan& pp, float2* psi, int n, int m, const ClauseLP* cl,
-                           const float2* ptab, const float2* btab, int K, unsigned* bar, int* err, int grid) {
+                           const float2* ptab, const float2* btab, int K, unsigned* bar, int* err, int grid,
+                           double* fold) {
   PersistArgs A;
+  A.fold = fold;
   A.psi = psi;
   A.cl = cl;
   A.ptab = ptab;
@@ -281,6 +299,7 @@ cudaError_t launch_persist(const LaunchCtx& lc, const PersistPlan& pp, float2* p
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persist_kernel, kPersistThreads, smem);
   if (e != cudaSuccess) return e;
   if (grid > occ * lc.num_sms) grid = occ * lc.num_sms;
+  if (grid > kFoldSlot - 1) grid = kFoldSlot - 1;  // one norm-fold partial per CTA
   if (grid < 1) return cudaErrorInvalidConfiguration;
   void* params[] = {&A};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(persist_kernel), dim3(grid), dim3(kPersistThreads),

@@ -282,14 +282,15 @@ void set_default_run_c(PassPlan& plan) {
 // the P phase at the boundary after step k (merged with the next step's first
 // half, or the last half at the end of the range): g round trips per step.
 static void build_rot_passes(const PassPlan& plan, long long k0, long long c0, long long c1, std::vector<Pass>& out) {
-  if (c0 == k0) out.push_back({kLpPhase, 0, 0, 0, 0, 0, 0});
+  if (c0 == k0) out.push_back({kLpPhase, 0, 0, 0, 0, 0, 0, -1});
   for (long long k = c0; k < c1; ++k) {
     const int brow = static_cast<int>(k - c0);
     for (size_t i = 0; i < plan.strided.size(); ++i) {
       const Group& g = plan.strided[i];
       out.push_back({kSpRot, g.a, g.q, 0, plan.run_c[i], brow, g.a2});
     }
-    out.push_back({plan.low_bits == 12 ? kLpRot12 : kLpRot, 0, 0, static_cast<int>(k + 1 - c0), 0, brow, 0});
+    out.push_back({plan.low_bits == 12 ? kLpRot12 : kLpRot, 0, 0, static_cast<int>(k + 1 - c0), 0, brow, 0,
+                   static_cast<int>(k - k0)});
   }
 }
 
@@ -316,16 +317,17 @@ void build_passes(const PassPlan& plan, long long k0, long long k1, long long c0
       if (i != pg) other(i);
   };
   if (c0 == k0) {
-    out.push_back({kLpFirst, 0, 0, 0, 0, 0, 0});
+    out.push_back({kLpFirst, 0, 0, 0, 0, 0, 0, -1});
     up();
   }
   for (long long k = c0; k < c1; ++k) {
     out.push_back({kSpWBW, top.a, top.q, 0, plan.run_c[pg], static_cast<int>(k - c0), top.a2});
     down();
+    const int rel = static_cast<int>(k - k0);
     if (k == k1 - 1) {
-      out.push_back({kLpLast, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0});
+      out.push_back({kLpLast, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0, rel});
     } else {
-      out.push_back({kLpMerge, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0});
+      out.push_back({kLpMerge, 0, 0, static_cast<int>(k + 1 - c0), 0, 0, 0, rel});
       up();
     }
   }
@@ -373,11 +375,14 @@ cudaError_t allow_smem(const void* func, size_t bytes) {
 }
 
 cudaError_t launch_planned_pass(const LaunchCtx& lc, const PassPlan& plan, const Pass& p, float2* psi, int m,
-                                const ClauseLP* cl, const float2* ptab, const float2* btab, int* err, const unsigned* counts) {
-  if (plan.wht_kind == kRotationForm) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err, counts);
-  if (plan.wht_kind) return launch_pass_tc(lc, p, psi, plan.n, m, cl, ptab, btab, plan.wht_kind == 1 ? 3 : 2);
-  if (plan.use_tma) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err, counts);
-  return launch_pass(lc, p, psi, plan.n, m, cl, ptab, btab);
+                                const ClauseLP* cl, const float2* ptab, const float2* btab, int* err, const unsigned* counts,
+                                double* fold) {
+  const NormFold nf = fold_for(fold, p);
+  if (plan.wht_kind == kRotationForm) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err, counts, nf);
+  if (plan.wht_kind)
+    return launch_pass_tc(lc, p, psi, plan.n, m, cl, ptab, btab, plan.wht_kind == 1 ? 3 : 2, err, counts, nf);
+  if (plan.use_tma) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err, counts, nf);
+  return launch_pass(lc, p, psi, plan.n, m, cl, ptab, btab, nf);
 }
 
 }  // namespace qaa

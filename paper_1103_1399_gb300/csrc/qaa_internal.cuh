@@ -65,7 +65,51 @@ struct Pass {
   int run_c;  // strided passes: 4 = 128-byte contiguous runs per tile row, 0 = default
   int brow;   // popcount-phase row (kSpWBW)
   int a2;     // strided passes: index bit of active bits 5..q-1 (a + 5 for a contiguous group)
+  // low passes: the step this pass ends, counted from the start of the range
+  // (-1 for the first pass of a range, -2 for no norm fold); selects the
+  // norm-fold slots below
+  int rel = -2;
 };
+
+// ---- norm fold ---------------------------------------------------------------
+// The exact evolution is unitary, but the FP32 state's norm performs a random
+// walk of roundings (about 4e-6 after 3200 Strang steps at 20 qubits, most of it
+// from the rounding of the few large amplitudes, so that the ground-state
+// probability drifts with it).  Every low pass therefore also sums |psi|^2 of
+// its output (FP32 per 1024-amplitude tile, FP64 beyond, one partial per CTA),
+// and the next step's low pass multiplies its P row by
+//   c = sqrt(N_ref 2^j / N),
+// N the previous step's sum, N_ref the sum taken by the first pass of the range
+// and 2^j the power of two nearest to N / N_ref (the unnormalised
+// Walsh-Hadamard stages and the 2^-n factor scale the norm by exact powers of
+// two between passes).  Each correction restores the norm the range started
+// with up to that step's rounding, so the corrections do not accumulate.
+// Slots of kFoldSlot doubles: [0] = number of partials, then one per CTA.
+// Slot 0 holds the range's reference, slots 1 and 2 alternate by step.
+constexpr int kFoldSlot = 2048;
+constexpr size_t kFoldBytes = 3 * kFoldSlot * sizeof(double);
+struct NormFold {
+  double* out = nullptr;         // slot this launch writes (null: none)
+  double* out2 = nullptr;        // a second slot written with the same partials
+  const double* ref = nullptr;   // the range's reference slot (null: no correction)
+  const double* prev = nullptr;  // the previous step's slot
+};
+// Slots of a low pass with relative step p.rel: the first pass writes the
+// reference and the slot its first merged step reads; step r reads the slot of
+// step r - 1 and writes its own.
+__host__ __device__ inline NormFold fold_for(double* base, const Pass& p) {
+  NormFold f;
+  if (!base || p.rel < -1) return f;
+  if (p.rel == -1) {
+    f.out = base;
+    f.out2 = base + 2 * kFoldSlot;
+    return f;
+  }
+  f.out = base + (1 + (p.rel & 1)) * kFoldSlot;
+  f.ref = base;
+  f.prev = base + (1 + ((p.rel + 1) & 1)) * kFoldSlot;
+  return f;
+}
 
 // ---- kernel launchers (defined in the .cu files) ----------------------------
 struct LaunchCtx {
@@ -82,7 +126,7 @@ cudaError_t launch_tables(const LaunchCtx& lc, float2* ptab, float2* btab, int n
                           const double* s_dev, long long K, long long k0, long long k1, long long c0, long long c1,
                           bool rot = false, const double* dt_dev = nullptr);
 cudaError_t launch_pass(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m,
-                        const ClauseLP* cl, const float2* ptab, const float2* btab);
+                        const ClauseLP* cl, const float2* ptab, const float2* btab, const NormFold& nf = NormFold());
 // Launch-graph helpers: phase rows from the same entry functions as
 // launch_tables (P positions p_first + j -> rows dst_p0 + j, B steps k_first + j
 // -> rows j, both offset by *ctr when ctr is non-null), and the loop-body tail
@@ -116,8 +160,15 @@ cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, con
 // Observables: partials has room for obs_partials_len(n) doubles; result is 5 doubles
 // {norm, <H_P>, ground_prob, ground_count, sum of pair correlations} on the device.
 size_t obs_partials_len(int n, int num_sms);
+// counts (optional): the stored per-tile clause counts of launch_lp_counts.
+// err: the bounded-wait error word of the TMA correlation passes.
 cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, int m,
-                               const ClauseLP* cl, double* partials, double* result);
+                               const ClauseLP* cl, double* partials, double* result,
+                               const unsigned* counts = nullptr, int* err = nullptr);
+// Read-only TMA pass: pair correlations of index bits [a, a+q) (5 <= q <= 10),
+// one partial per CTA in partials[0 .. nparts).
+cudaError_t launch_corr_tma(const LaunchCtx& lc, const float2* psi, int n, int a, int q, double* partials, int nparts,
+                            int* err);
 
 // TMA-pipelined variants of the streaming passes (tma_kernels.cu).  err is a
 // device word set to nonzero when a bounded wait expires.  psi must be 16-byte
@@ -128,17 +179,22 @@ bool tma_available();
 // Bytes per contiguous tile row of a q-bit TMA strided pass (run_c as in Pass).
 int tma_run_bytes(int q, int run_c);
 cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
-                            const float2* ptab, const float2* btab, int* err, const unsigned* counts = nullptr);
+                            const float2* ptab, const float2* btab, int* err, const unsigned* counts = nullptr,
+                            const NormFold& nf = NormFold());
 // Per-tile bit-sliced violated-clause counts of every 1024-amplitude tile
 // (lp_counts_bytes(n) bytes), computed once per instance.
 size_t lp_counts_bytes(int n);
 cudaError_t launch_lp_counts(const LaunchCtx& lc, unsigned* counts, int n, int m, const ClauseLP* cl);
 
 // Tensor-core variant (tc_kernels.cu): the Walsh-Hadamard transforms of every
-// streaming pass as 16 x 16 Hadamard blocks on BF16-split operands (parts = 3:
-// hi + mid + lo, parts = 2: hi + lo) with FP32 accumulation.
+// streaming pass of the W.B.W form as 5-bit stages of tcgen05 GEMMs against
+// H_32 on BF16-split operands (parts = 3: hi + mid + lo, parts = 2: hi + lo)
+// with FP32 accumulation in tensor memory.  The low passes need n >= 13 and
+// the stored per-tile counts; err is the bounded-wait error word.
 cudaError_t launch_pass_tc(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
-                           const float2* ptab, const float2* btab, int parts);
+                           const float2* ptab, const float2* btab, int parts, int* err, const unsigned* counts,
+                           const NormFold& nf = NormFold());
+size_t tc_smem_bytes(int parts);
 
 // Persistent evolution of one instance with 15 <= n <= 24 in one cooperative
 // launch (persist.cu): every pass of every step inside the kernel, separated by
@@ -150,7 +206,8 @@ struct PersistPlan {
   int ga[3], gq[3];
 };
 cudaError_t launch_persist(const LaunchCtx& lc, const PersistPlan& pp, float2* psi, int n, int m, const ClauseLP* cl,
-                           const float2* ptab, const float2* btab, int K, unsigned* bar, int* err, int grid);
+                           const float2* ptab, const float2* btab, int K, unsigned* bar, int* err, int grid,
+                           double* fold = nullptr);
 
 // Lanczos on H(s) (lanczos.cu): `iters` iterations from the uniform state or a
 // seeded random real vector; alpha[0..iters), beta[0..iters] (beta[0] = 0) in

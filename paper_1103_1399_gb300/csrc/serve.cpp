@@ -113,6 +113,7 @@ struct Req {
   std::vector<qaa::ClauseLP> lp;
   qaa::PassPlan plan;
   double t_submit = 0, t_admit = -1, t_done = -1;
+  double t_dev_start = -1, t_dev_end = -1;  // device clock, seconds since the server's reference event
   int status = QAA_PENDING;
   double res[5] = {0, 0, 0, 0, 0};
   Phase phase = kQueued;
@@ -131,7 +132,9 @@ struct Req {
   unsigned* d_bar = nullptr;
   unsigned* d_counts = nullptr;  // stored per-tile clause counts (streamed requests), else null
   size_t counts_bytes = 0;
+  double* d_fold = nullptr;  // norm-fold slots of the low passes (streamed and persistent requests)
   cudaEvent_t done_ev = nullptr;
+  cudaEvent_t start_ev = nullptr;  // recorded before the request's first device work
   cudaGraphExec_t gexec = nullptr;  // launch graph of a streamed request, kept until it completes
   bool persist = false;  // mid-size: one persistent cooperative launch for the whole run
   bool graph = false;    // streamed: one launch graph for the whole run
@@ -148,10 +151,12 @@ size_t table_bytes(int n, int m, long long K, bool whole_run, bool graph) {
 }
 
 // Device bytes of one request: state, clause tables, phase tables, reduction
-// partials, results, an error word and a grid-barrier word pair.
+// partials, results, an error word, a grid-barrier word pair and, beyond the
+// on-chip sizes, the low passes' norm-fold slots.
 size_t request_bytes(int n, int m, size_t tab_bytes, size_t counts_bytes, int num_sms) {
   size_t b = align_up((static_cast<size_t>(8) << n));
   b += align_up(counts_bytes);
+  if (n > qaa::kOnchipMaxBits) b += align_up(qaa::kFoldBytes);
   b += align_up(16u * static_cast<size_t>(std::max(m, 1))) * 2;
   b += align_up(tab_bytes);
   b += align_up(8u * qaa::obs_partials_len(n, num_sms));
@@ -174,6 +179,7 @@ struct qaa_server {
   double* h_res = nullptr;  // pinned, 8 doubles per slot
   unsigned char* h_stage = nullptr;  // pinned clause-table staging, kStageBytes per slot
   double t0 = 0;
+  cudaEvent_t ref_ev = nullptr;  // device-clock origin of the requests' device intervals
   // submission (guarded by mu)
   std::mutex mu;
   std::condition_variable cv;
@@ -230,6 +236,10 @@ void release(qaa_server* s, Req* r) {
     cudaEventDestroy(r->done_ev);
     r->done_ev = nullptr;
   }
+  if (r->start_ev) {
+    cudaEventDestroy(r->start_ev);
+    r->start_ev = nullptr;
+  }
   if (r->gexec) {
     cudaGraphExecDestroy(r->gexec);
     r->gexec = nullptr;
@@ -271,6 +281,7 @@ bool place(qaa_server* s, Req* r) {
   r->d_err = reinterpret_cast<int*>(take(16));
   r->d_bar = reinterpret_cast<unsigned*>(take(16));
   r->d_counts = r->counts_bytes ? reinterpret_cast<unsigned*>(take(r->counts_bytes)) : nullptr;
+  r->d_fold = r->n > qaa::kOnchipMaxBits ? reinterpret_cast<double*>(take(qaa::kFoldBytes)) : nullptr;
   return true;
 }
 
@@ -292,20 +303,29 @@ cudaError_t upload_tables(qaa_server* s, Req* r, cudaStream_t st) {
 // the completion event.
 cudaError_t observe_async(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
-  cudaError_t e = qaa::launch_observables(lc, r->psi, r->n, r->m, r->d_lp, r->d_part, r->d_res);
+  cudaError_t e = qaa::launch_observables(lc, r->psi, r->n, r->m, r->d_lp, r->d_part, r->d_res, r->d_counts, r->d_err);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->h_res + 8 * r->slot, r->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_res + 8 * r->slot + 5, r->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&r->done_ev);  // timed: the end of the request's device interval
   if (e == cudaSuccess) e = cudaEventRecord(r->done_ev, st);
   return e;
 }
 
 // The streaming evolution of one request (issuer thread, its own stream):
 // one launch graph for the whole run, or one launch per pass.
+// The start of a request's device interval: an event on its stream ahead of
+// its first copy or kernel.
+cudaError_t mark_start(Req* r, cudaStream_t st) {
+  cudaError_t e = cudaEventCreate(&r->start_ev);
+  if (e == cudaSuccess) e = cudaEventRecord(r->start_ev, st);
+  return e;
+}
+
 cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
-  cudaError_t e = upload_tables(s, r, st);
+  cudaError_t e = mark_start(r, st);
+  if (e == cudaSuccess) e = upload_tables(s, r, st);
   if (e == cudaSuccess) e = qaa::launch_init_uniform(lc, r->psi, r->n);
   if (e == cudaSuccess && r->d_counts) e = qaa::launch_lp_counts(lc, r->d_counts, r->n, r->m, r->d_lp);
   const double dt = r->T / static_cast<double>(r->K);
@@ -322,6 +342,7 @@ cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
     gs.k1 = r->K;
     gs.num_sms = s->num_sms;
     gs.counts = r->d_counts;
+    gs.fold = r->d_fold;
     qaa::graph_scratch_split(r->d_tab, r->m, gs);
     if (e == cudaSuccess) e = qaa::build_evolve_graph(gs, &r->gexec);
     if (e == cudaSuccess) e = cudaGraphLaunch(r->gexec, st);
@@ -338,7 +359,8 @@ cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
     qaa::build_passes(r->plan, 0, r->K, c0, c1, passes);
     for (const qaa::Pass& ps : passes) {
       if (e != cudaSuccess) break;
-      e = qaa::launch_planned_pass(lc, r->plan, ps, r->psi, r->m, r->d_lp, ptab, btab, r->d_err, r->d_counts);
+      e = qaa::launch_planned_pass(lc, r->plan, ps, r->psi, r->m, r->d_lp, ptab, btab, r->d_err, r->d_counts,
+                                   r->d_fold);
     }
   }
   if (e == cudaSuccess) e = observe_async(s, r, st);
@@ -349,7 +371,8 @@ cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
 // launch on a few CTAs, so several such requests share the GPU at once.
 cudaError_t issue_persistent(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
-  cudaError_t e = upload_tables(s, r, st);
+  cudaError_t e = mark_start(r, st);
+  if (e == cudaSuccess) e = upload_tables(s, r, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(r->d_bar, 0, 2 * sizeof(unsigned), st);
   // injected fault: the arrival count starts at 2^32 - 1, so the first grid
   // barrier never sees all CTAs arrive; they give up after the bound, record
@@ -371,7 +394,7 @@ cudaError_t issue_persistent(qaa_server* s, Req* r, cudaStream_t st) {
   const int grid = static_cast<int>(std::min<long long>(1ll << std::max(r->n - 13, 0), s->persist_grid));
   if (e == cudaSuccess)
     e = qaa::launch_persist(lc, pp, r->psi, r->n, r->m, r->d_lp, ptab, btab, static_cast<int>(r->K), r->d_bar,
-                            r->d_err, grid);
+                            r->d_err, grid, r->d_fold);
   if (e == cudaSuccess) e = observe_async(s, r, st);
   return e;
 }
@@ -416,7 +439,8 @@ bool launch_batch(qaa_server* s, std::vector<Req*>& small) {
   int nj = 0;
   cudaError_t e = cudaSuccess;
   for (Req* r : small) {
-    e = upload_tables(s, r, s->batch_stream);
+    e = mark_start(r, s->batch_stream);
+    if (e == cudaSuccess) e = upload_tables(s, r, s->batch_stream);
     const double dt = r->T / static_cast<double>(r->K);
     float2* ptab = r->d_tab;
     float2* btab = r->d_tab + static_cast<size_t>(r->K + 1) * (r->m + 1);
@@ -553,6 +577,14 @@ void worker_main(qaa_server* s) {
       }
       std::lock_guard<std::mutex> lk(s->mu);
       if (r->status == QAA_PENDING) {
+        float a = 0.f, b = 0.f;
+        if (r->start_ev && r->done_ev && cudaEventElapsedTime(&a, s->ref_ev, r->start_ev) == cudaSuccess &&
+            cudaEventElapsedTime(&b, s->ref_ev, r->done_ev) == cudaSuccess) {
+          r->t_dev_start = 1e-3 * a;
+          r->t_dev_end = 1e-3 * b;
+        } else {
+          cudaGetLastError();
+        }
         std::memcpy(r->res, s->h_res + 8 * r->slot, 5 * sizeof(double));
         int err = 0;
         std::memcpy(&err, s->h_res + 8 * r->slot + 5, sizeof(int));
@@ -586,6 +618,7 @@ int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) 
       if (s->jobs_ev[t]) cudaEventDestroy(s->jobs_ev[t]);
     }
     if (s->batch_stream) cudaStreamDestroy(s->batch_stream);
+    if (s->ref_ev) cudaEventDestroy(s->ref_ev);
     for (cudaStream_t st : s->issue_streams) cudaStreamDestroy(st);
     for (cudaStream_t st : s->persist_streams) cudaStreamDestroy(st);
     cudaGetLastError();
@@ -647,6 +680,11 @@ int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) 
       return bail(QAA_E_CUDA, "cannot create streams");
     s->persist_streams.push_back(st);
   }
+  // the device clock's origin for the requests' device intervals: recorded
+  // (and complete) before any request is issued
+  if (cudaEventCreate(&s->ref_ev) != cudaSuccess || cudaEventRecord(s->ref_ev, s->batch_stream) != cudaSuccess ||
+      cudaEventSynchronize(s->ref_ev) != cudaSuccess)
+    return bail(QAA_E_CUDA, "cannot record the reference event");
   s->t0 = steady_now();
   for (int i = 0; i < nissuers; ++i) s->issuers.emplace_back(issuer_main, s, i);
   s->worker = std::thread(worker_main, s);
@@ -732,6 +770,8 @@ int qaa_poll(qaa_server* s, uint64_t ticket, qaa_result* out) {
   out->t_submit = r->t_submit;
   out->t_admit = r->t_admit;
   out->t_done = r->t_done;
+  out->t_dev_start = r->t_dev_start;
+  out->t_dev_end = r->t_dev_end;
   out->n = r->n;
   out->steps = r->K;
   out->status = r->status;
@@ -801,6 +841,7 @@ int qaa_server_destroy(qaa_server* s) {
   }
   cudaStreamSynchronize(s->batch_stream);
   cudaStreamDestroy(s->batch_stream);
+  cudaEventDestroy(s->ref_ev);
   for (int t = 0; t < 2; ++t) {
     cudaFreeHost(s->h_jobs[t]);
     cudaFree(s->d_jobs[t]);
@@ -811,6 +852,7 @@ int qaa_server_destroy(qaa_server* s) {
   cudaFreeHost(s->h_stage);
   for (auto& kv : s->all) {
     if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
+    if (kv.second->start_ev) cudaEventDestroy(kv.second->start_ev);
     if (kv.second->gexec) cudaGraphExecDestroy(kv.second->gexec);
     delete kv.second;
   }

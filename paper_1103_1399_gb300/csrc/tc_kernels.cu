@@ -1,391 +1,564 @@
-// Tensor-core variant of the streaming passes: every Walsh-Hadamard transform
-// over a group of index bits is applied as 16 x 16 Hadamard blocks on the
-// tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation) instead
-// of FP32 butterflies.  The complex64 amplitudes are split exactly enough into
-// BF16 parts, x = hi + mid + lo (three products, ~FP32 accuracy) or x = hi + lo
-// (two products, ~16 mantissa bits); the +-1 Hadamard entries are exact in
-// BF16, so only the splitting and the FP32 accumulation round.
+// Tensor-core variant of the W.B.W form's passes on the fifth-generation tensor
+// cores (tcgen05.mma, accumulators in tensor memory).
 //
-// One MMA stage transforms 4 index bits K of a shared-memory tile.  The A
-// operand holds data: row g (g = lane / 4) is the real part, row g + 8 the
-// imaginary part, of the amplitude whose 3 "other" bits O equal g; column k is
-// the value of the K bits.  B is the Hadamard block (two 16 x 8 halves).  With
-// the m16n8k16 fragment layouts, lane (g, t = lane % 4) supplies the inputs at
-// k = 2t, 2t+1, 2t+8, 2t+9 and receives the outputs at exactly those k, so a
-// stage works in place: 4 shared loads, the split, 6 (or 4) MMAs, 4 stores per
-// lane and block of 16 x 8 amplitudes.  A stage may apply the Hadamard to a
-// subset of K only (identity on the rest), which covers groups whose size is
-// not a multiple of 4.
+// Every Walsh-Hadamard transform over a group of up to 10 index bits is applied
+// as at most two stages of 5 bits, each stage one GEMM against the 32 x 32
+// Hadamard block H_32 (entries +-1, exact in BF16):
+//   D[row][k'] = sum_k A[row][k] H_32[k][k'],
+// a row being the 32 amplitudes (real or imaginary parts) that differ only in
+// the stage's 5 bits.  The complex64 amplitudes are split into BF16 parts,
+// x = hi + mid + lo (three products, about FP32 accuracy) or x = hi + lo (two
+// products, about 16 mantissa bits); only the split and the FP32 accumulation
+// round.  The hi part and the small parts accumulate in separate tensor-memory
+// accumulators (the tensor cores' FP32 accumulation drops low-order bits of
+// small addends added to a large accumulator) and are added in FP32 when read
+// back.
 //
-// Tiles are read and written with plain coalesced loads/stores and staged in
-// shared memory under an XOR swizzle of the low address bits chosen so that
-// every stage's access pattern, and the load/store layouts, touch 16 distinct
-// bank pairs per warp access (the minimum for 8-byte elements).
-#include <cuda_bf16.h>
+// A CTA (256 threads, one per SM) owns a tile of 8192 amplitudes in shared
+// memory: 2^Q rows of a strided group (Q <= 10) by 2^(13-Q) contiguous
+// amplitudes, loaded by a cp.async.bulk.tensor box; or, for the low pass
+// (bits 0..9), eight consecutive 1024-amplitude tiles loaded with cp.async.
+// Tile index u (13 bits): stage 1 takes its K from a 5-bit field of u and
+// stage 2 from u bits 8..12; the other 8 bits and re/im form 512 rows, four
+// M = 128 units (two per component).  Per stage each thread reads its row's 32
+// values from the tile, splits them and writes the BF16 parts in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
+// LBO = 128 B along K, SBO = 512 B along M); one thread issues the MMAs
+// (M = 128, N = 32, K = 16 each) and commits them to an mbarrier; every
+// thread then reads its row's accumulators with tcgen05.ld (its warp's lane
+// quarter) and writes the results back to the tile or, after the last stage,
+// straight to global memory.  The phases between transforms (the popcount
+// phase B, the merged P phase of the low pass, with the norm fold of the
+// previous step) are applied on the way.  The next tile's load is issued as
+// soon as the last stage has read the tile.
+//
+// Every mbarrier wait is bounded; on expiry the kernel records the handle's
+// error word and all threads leave together, releasing tensor memory.
+#include <cuda.h>
+
+#include <cstring>
 
 #include "device_common.cuh"
 
 namespace qaa {
 
-// ---------------------------------------------------------------- MMA -------
-__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
-  const unsigned short a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
-  const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
-  return static_cast<unsigned>(a) | (static_cast<unsigned>(b) << 16);
-}
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+namespace {
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+// ---------------------------------------------------------------- PTX -------
+__device__ __forceinline__ uint32_t tc_smem(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void tc_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void tc_mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool tc_mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(tc_smem(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr long long kTcWaitLimit = 1ll << 24;
+__device__ __forceinline__ bool tc_mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kTcWaitLimit; ++it)
+    if (tc_mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tc_fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                               int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(tc_smem(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(tc_smem(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void tc_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tc_cp_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// tensor memory: allocation by one whole warp, the address written to shared memory
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// D (tensor memory) = A B^T (+ D when acc), A and B described in shared memory
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem(bar))
+               : "memory");
+}
+// 32 consecutive FP32 columns of the calling thread's lane (its warp's quarter);
+// the wait is in the same asm statement, so no use of the registers can be
+// scheduled before the load has completed
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Hadamard block restricted to the bits in `hmask` (identity on the other K
-// bits): M[k][k'] = prod_{b in hmask} (-1)^(k_b k'_b) * prod_{b not in hmask} [k_b == k'_b].
-__device__ __forceinline__ float hblock(int k, int kp, int hmask) {
-  if (((k ^ kp) & ~hmask & 15) != 0) return 0.0f;
+// two FP32 values rounded to BF16 and packed (the first in the low half)
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t p) { return __uint_as_float(p & 0xffff0000u); }
+
+// ------------------------------------------------------------ geometry ------
+constexpr int kTcThreads = 256;
+constexpr int kTcTile = 8192;          // amplitudes per CTA tile
+constexpr int kTcUnitBytes = 8192;     // one 128 x 32 BF16 operand unit
+constexpr int kTcCols = 256;           // tensor-memory columns: 4 units x (hi 32 + small 32)
+constexpr int kTcEStride = 33;         // energy buffer rows (padded)
+constexpr uint32_t kTcLBO = 128, kTcSBO = 512;
+// instruction descriptor: D F32, A and B BF16, both K-major, N = 32, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct TcLayout {
+  size_t off_a, off_h, off_e, off_pt, off_bt, off_bar, total;
+  __host__ __device__ explicit TcLayout(int parts) {
+    off_a = static_cast<size_t>(kTcTile) * 8;
+    off_h = off_a + static_cast<size_t>(parts) * 4 * kTcUnitBytes;
+    off_e = off_h + 2 * 2048;
+    off_pt = off_e + 8 * 32 * kTcEStride * 2;
+    off_pt = (off_pt + 15) & ~static_cast<size_t>(15);
+    off_bt = off_pt + 8 * (QAA_MAX_CLAUSES_DEV + 1);
+    off_bar = off_bt + 64 * 8;
+    total = off_bar + 32;
+  }
+};
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(kTcLBO >> 4) << 16) |
+         (static_cast<uint64_t>(kTcSBO >> 4) << 32) | (1ull << 46);
+}
+
+// Tile index u of (row R, K index k) in stage 1 (K = u bits C..C+4) and stage 2
+// (K = u bits 8..12).
+__device__ __forceinline__ int u_stage1(int R, int k, int C) {
+  return (R & ((1 << C) - 1)) | (k << C) | ((R >> C) << (C + 5));
+}
+__device__ __forceinline__ int u_stage2(int R, int k) { return (R & 255) | (k << 8); }
+// Shared-memory slot of u: the low pass's tile is XOR-swizzled on bits 0..3 by
+// bits 5..8 so that its loads and both stages' row accesses are conflict free;
+// the strided tile is dense (as the TMA box writes it).
+template <bool LOW>
+__device__ __forceinline__ int tslot(int u) {
+  return LOW ? (u ^ ((u >> 5) & 15)) : u;
+}
+
+// Hadamard block restricted to the K bits in hmask (identity on the others).
+__device__ __forceinline__ float hentry(int k, int kp, int hmask) {
+  if (((k ^ kp) & ~hmask & 31) != 0) return 0.0f;
   return (__popc(k & kp & hmask) & 1) ? -1.0f : 1.0f;
 }
 
-struct HFrag {
-  unsigned b[2][2];  // [half][reg]
-  __device__ __forceinline__ void init(int hmask, int lane) {
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int col = 8 * h + g;
-      b[h][0] = pack_bf16(hblock(2 * t, col, hmask), hblock(2 * t + 1, col, hmask));
-      b[h][1] = pack_bf16(hblock(2 * t + 8, col, hmask), hblock(2 * t + 9, col, hmask));
-    }
-  }
-};
+}  // namespace
 
-// In-place transform of one 16 (K) x 8 (O) block of complex amplitudes.
-// p[q] (q = 0..3) points at the amplitude with k = 2t, 2t+1, 2t+8, 2t+9.
-// The tensor cores' FP32 accumulation drops low-order bits when small products
-// are aligned to a large accumulator (a bias toward zero), so the hi part and
-// the small parts (lo first, then mid) accumulate separately and are combined
-// with one round-to-nearest FP32 addition.
-template <int PARTS>
-__device__ __forceinline__ void tc_block(float2* p0, float2* p1, float2* p2, float2* p3, const HFrag& H) {
-  const float2 x0 = *p0, x1 = *p1, x2 = *p2, x3 = *p3;
-  const float re[4] = {x0.x, x1.x, x2.x, x3.x}, im[4] = {x0.y, x1.y, x2.y, x3.y};
-  float part_r[PARTS][4], part_i[PARTS][4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float rr = re[q], ri = im[q];
-#pragma unroll
-    for (int p = 0; p < PARTS; ++p) {
-      part_r[p][q] = (p == PARTS - 1) ? rr : bf16_round(rr);
-      part_i[p][q] = (p == PARTS - 1) ? ri : bf16_round(ri);
-      rr -= part_r[p][q];  // exact: the remainder of a round-to-nearest in FP32
-      ri -= part_i[p][q];
-    }
-  }
-  float h0[4] = {0.f, 0.f, 0.f, 0.f}, h1[4] = {0.f, 0.f, 0.f, 0.f};  // hi part
-  float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};  // small parts
-#pragma unroll
-  for (int p = PARTS - 1; p >= 0; --p) {
-    // rows g (real) and g + 8 (imaginary); columns 2t, 2t+1 | 2t+8, 2t+9
-    const unsigned a[4] = {pack_bf16(part_r[p][0], part_r[p][1]), pack_bf16(part_i[p][0], part_i[p][1]),
-                           pack_bf16(part_r[p][2], part_r[p][3]), pack_bf16(part_i[p][2], part_i[p][3])};
-    if (p == 0) {
-      mma_bf16(h0, a, H.b[0][0], H.b[0][1]);
-      mma_bf16(h1, a, H.b[1][0], H.b[1][1]);
-    } else {
-      mma_bf16(s0, a, H.b[0][0], H.b[0][1]);
-      mma_bf16(s1, a, H.b[1][0], H.b[1][1]);
-    }
-  }
-  *p0 = make_float2(h0[0] + s0[0], h0[2] + s0[2]);
-  *p1 = make_float2(h0[1] + s0[1], h0[3] + s0[3]);
-  *p2 = make_float2(h1[0] + s1[0], h1[2] + s1[2]);
-  *p3 = make_float2(h1[1] + s1[1], h1[3] + s1[3]);
-}
-
-// ------------------------------------------------------- low pass (TC) ------
-// Tile = 1024 consecutive amplitudes, one warp.  Stages: K = bits 0..3 (O =
-// 4..6), K = bits 4..7 (O = 0..2), K = bits 6..9 with the Hadamard on 8, 9 only
-// (O = 0..2).  Swizzle: address bits 0..3 XOR (t9^t4, t6, t7, t5^t8).
-__device__ __forceinline__ int lp_swz(int t) {
-  const int a0 = ((t >> 4) ^ (t >> 9)) & 1, a1 = (t >> 6) & 1, a2 = (t >> 7) & 1, a3 = ((t >> 5) ^ (t >> 8)) & 1;
-  return t ^ (a0 | (a1 << 1) | (a2 << 2) | (a3 << 3));
-}
-
-template <int PARTS>
-__device__ __forceinline__ void lp_tc_transform(float2* __restrict__ s, int lane, const HFrag& H4, const HFrag& H2) {
-  const int g = lane >> 2, t = lane & 3;
-  const int ks[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
-  // stage 1: K = bits 0..3, O = bits 4..6, blocks = bits 7..9
-#pragma unroll 1
-  for (int blk = 0; blk < 8; ++blk) {
-    const int base = (g << 4) | (blk << 7);
-    tc_block<PARTS>(s + lp_swz(base | ks[0]), s + lp_swz(base | ks[1]), s + lp_swz(base | ks[2]),
-                    s + lp_swz(base | ks[3]), H4);
-  }
-  __syncwarp();
-  // stage 2: K = bits 4..7, O = bits 0..2, blocks = bits 3, 8, 9
-#pragma unroll 1
-  for (int blk = 0; blk < 8; ++blk) {
-    const int base = g | ((blk & 1) << 3) | ((blk >> 1) << 8);
-    tc_block<PARTS>(s + lp_swz(base | (ks[0] << 4)), s + lp_swz(base | (ks[1] << 4)), s + lp_swz(base | (ks[2] << 4)),
-                    s + lp_swz(base | (ks[3] << 4)), H4);
-  }
-  __syncwarp();
-  // stage 3: K = bits 6..9 (Hadamard on bits 8, 9), O = bits 0..2, blocks = bits 3..5
-#pragma unroll 1
-  for (int blk = 0; blk < 8; ++blk) {
-    const int base = g | (blk << 3);
-    tc_block<PARTS>(s + lp_swz(base | (ks[0] << 6)), s + lp_swz(base | (ks[1] << 6)), s + lp_swz(base | (ks[2] << 6)),
-                    s + lp_swz(base | (ks[3] << 6)), H2);
-  }
-  __syncwarp();
-}
-
-constexpr int kTcWarps = 8;
-
-template <int KIND, int PARTS>
-__global__ void __launch_bounds__(kTcWarps * 32)
-    lp_tc_kernel(float2* __restrict__ psi, int m, const ClauseLP* __restrict__ cl, const float2* __restrict__ prow,
-                 long long ntiles) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
-  float2* s_pt = reinterpret_cast<float2*>(smem + 16 * m);
-  const size_t off = 16u * m + ((8u * (m + 1) + 15u) & ~15u);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* s_tile = reinterpret_cast<float2*>(smem + off) + warp * kLowTile;
-  uint2* s_act = reinterpret_cast<uint2*>(smem + off + 8u * kLowTile * kTcWarps) + warp * (m + 16);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
-  for (int i = threadIdx.x; i <= m; i += blockDim.x) s_pt[i] = prow[i];
-  __syncthreads();
-  HFrag H4, H2;
-  H4.init(15, lane);
-  H2.init(12, lane);  // bits 8, 9 are K bits 2, 3 of stage 3
-
-  const long long step = static_cast<long long>(gridDim.x) * kTcWarps;
-  for (long long tile = static_cast<long long>(blockIdx.x) * kTcWarps + warp; tile < ntiles; tile += step) {
-    float2* g = psi + (tile << kLowBits);
-    int nconst, npad;
-    unsigned pl[kPlanes];
-    __syncwarp();
-    // P is applied with the registers holding bits 5..9 (layout X), as in the first low pass.
-    fold_tile<false>(s_cl, m, static_cast<unsigned>(tile), lane, s_act, nconst, npad);
-    count_active(s_act, npad, 1u << lane, pl);
-    float2 v[32];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] = g[lane + 32 * r];
-    if (KIND == kLpFirst) apply_p_phase(v, pl, nconst, s_pt);
-#pragma unroll
-    for (int r = 0; r < 32; ++r) s_tile[lp_swz(lane + 32 * r)] = v[r];
-    __syncwarp();
-    lp_tc_transform<PARTS>(s_tile, lane, H4, H2);
-    if (KIND != kLpFirst) {
-#pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = s_tile[lp_swz(lane + 32 * r)];
-      apply_p_phase(v, pl, nconst, s_pt);
-      if (KIND == kLpMerge) {
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < 32; ++r) s_tile[lp_swz(lane + 32 * r)] = v[r];
-        __syncwarp();
-        lp_tc_transform<PARTS>(s_tile, lane, H4, H2);
-      }
-    }
-    if (KIND != kLpLast) {
-#pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = s_tile[lp_swz(lane + 32 * r)];
-    }
-#pragma unroll
-    for (int r = 0; r < 32; ++r) g[lane + 32 * r] = v[r];
-  }
-}
-
-// -------------------------------------------------- strided pass (TC) -------
-// Tile t = j + (i << C): 2^Q rows i (active bits, i bits 0..4 at a1, 5..Q-1 at
-// a2) x 2^C contiguous amplitudes j (C >= 3).  Stage list over i bits:
-// [0,4) all new; [4,8) all new when Q >= 8; a last stage K = [Q-4, Q) with
-// the Hadamard on the bits not yet transformed.  O = j bits 0..2.  Swizzle:
-// address bit 3 XOR the parity of i bits in S, where S meets {b+1, b+2} of
-// every stage start b (those two K bits vary across the lanes).
-template <int Q, int C>
-struct TcSp {
-  static constexpr int NT = 256;
-  static constexpr int TILE = 1 << (Q + C);
-  static constexpr int S1 = 1, S2 = (Q >= 8) ? 5 : 1, S3 = (Q > 8 || (Q > 4 && Q < 8)) ? Q - 3 : 1;
-  __device__ __forceinline__ static int swz(int t) {
-    const int i = t >> C;
-    int par = (i >> S1) & 1;
-    if (S2 != S1) par ^= (i >> S2) & 1;
-    if (S3 != S1 && S3 != S2) par ^= (i >> S3) & 1;
-    return t ^ (par << 3);
-  }
-};
-
-template <int Q, int C, int PARTS>
-__device__ __forceinline__ void sp_tc_stage(float2* __restrict__ s, int b, const HFrag& H, int warp, int lane) {
-  using G = TcSp<Q, C>;
-  const int g = lane >> 2, t = lane & 3;
-  constexpr int nblk = (1 << (Q + C)) >> 7;  // 128 amplitudes per block
-  // block index enumerates j bits >= 3 and the i bits outside [b, b+4)
-#pragma unroll 1
-  for (int blk = warp; blk < nblk; blk += G::NT / 32) {
-    const int jhi = blk & ((1 << (C - 3)) - 1);
-    const int irest = blk >> (C - 3);  // Q-4 bits of i outside [b, b+4)
-    const int i_base = (irest & ((1 << b) - 1)) | ((irest >> b) << (b + 4));
-    const int base = g | (jhi << 3) | (i_base << C);
-    tc_block<PARTS>(s + G::swz(base | ((2 * t) << (b + C))), s + G::swz(base | ((2 * t + 1) << (b + C))),
-                    s + G::swz(base | ((2 * t + 8) << (b + C))), s + G::swz(base | ((2 * t + 9) << (b + C))), H);
-  }
-}
-
-template <int Q, int C, bool WBW, int PARTS>
-__global__ void __launch_bounds__(256)
-    sp_tc_kernel(float2* __restrict__ psi, int n, int a1, int a2, const float2* __restrict__ brow, long long ntiles) {
-  using G = TcSp<Q, C>;
+// KIND: kSpW, kSpWBW (strided, Q bits), kLpFirst, kLpMerge, kLpLast (low pass, Q = 10).
+template <int KIND, int Q, int PARTS>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_pass_kernel(float2* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, int n, int a1, int a2,
+                   long long ntiles, const float2* __restrict__ prow, const float2* __restrict__ brow,
+                   const unsigned* __restrict__ counts, int m, int* __restrict__ err, const NormFold nf) {
+  constexpr bool LOW = KIND == kLpFirst || KIND == kLpMerge || KIND == kLpLast;
+  constexpr int C = LOW ? 0 : 13 - Q;  // stage-1 K field starts at u bit C
   constexpr int QB = Q - 5;
-  extern __shared__ __align__(16) unsigned char smem[];
-  float2* s_tile = reinterpret_cast<float2*>(smem);
-  float2* s_bt = s_tile + G::TILE;
-  if (WBW) {
-    for (int i = threadIdx.x; i <= n; i += blockDim.x) s_bt[i] = brow[i];
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // stage list
-  constexpr int NST = (Q <= 4) ? 1 : ((Q <= 8 && Q != 8) ? 2 : ((Q == 8) ? 2 : 3));
-  int sb[3], hm[3];
-  sb[0] = 0;
-  hm[0] = 15;
-  if (Q == 8) {
-    sb[1] = 4;
-    hm[1] = 15;
-  } else if (Q < 8) {
-    sb[1] = Q - 4;
-    hm[1] = 15 & ~((1 << (8 - Q)) - 1);  // K bits >= 8-Q are the new bits 4..Q-1
-  } else {
-    sb[1] = 4;
-    hm[1] = 15;
-    sb[2] = Q - 4;
-    hm[2] = 15 & ~((1 << (12 - Q)) - 1);  // new bits 8..Q-1
-  }
-  HFrag H[3];
-#pragma unroll
-  for (int s = 0; s < NST; ++s) H[s].init(hm[s], lane);
+  constexpr bool TWO = Q > 5;          // two stages per transform (Q = 5: stage 2 alone)
+  constexpr int NW = (KIND == kSpWBW || KIND == kLpMerge) ? 2 : 1;  // transforms per tile
+  const TcLayout L(PARTS);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float2* s_t = reinterpret_cast<float2*>(smem);
+  unsigned char* s_a = smem + L.off_a;
+  unsigned char* s_h = smem + L.off_h;
+  uint16_t* s_e = reinterpret_cast<uint16_t*>(smem + L.off_e);
+  float2* s_pt = reinterpret_cast<float2*>(smem + L.off_pt);
+  float2* s_bt = reinterpret_cast<float2*>(smem + L.off_bt);
+  uint64_t* bar_tma = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  uint64_t* bar_mma = bar_tma + 1;
+  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(bar_tma + 2);
 
-  const int lo_bits = a1 - C, mid_bits = a2 - a1 - 5;
-  const unsigned long long lo_mask = (1ull << lo_bits) - 1ull, mid_mask = (1ull << mid_bits) - 1ull;
-  // load/store layout: thread (j, th = i bits 5..Q-1), register r = i bits 0..4
-  const int NTILE = 1 << (Q + C - 5);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q4 = warp & 3, hh = warp >> 2;
+  const int r = 32 * q4 + lane;  // tensor-memory lane = row within a unit
+  const int R = r + 128 * hh;    // row (without re/im), 0..255
+
+  // tensor memory, barriers, the two Hadamard operands (K-major, N x K)
+  if (warp == 0) tmem_alloc(s_taddr, kTcCols);
+  if (tid == 0) {
+    tc_mbar_init(bar_tma, 1);
+    tc_mbar_init(bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    const int hm2 = TWO ? (31 & ~((1 << (10 - Q)) - 1)) : 31;
+    for (int e = tid; e < 2 * 32 * 16; e += kTcThreads) {
+      const int s = e >> 9, nn = (e >> 4) & 31, kp = (e & 15) * 2;  // operand s, row n, columns kp, kp+1
+      const int hm = s == 0 ? 31 : hm2;
+      const uint32_t w = bf16x2(hentry(kp, nn, hm), hentry(kp + 1, nn, hm));
+      const uint32_t off = s * 2048 + (nn >> 3) * kTcSBO + (kp >> 3) * kTcLBO + (nn & 7) * 16 + (kp & 7) * 2;
+      *reinterpret_cast<uint32_t*>(s_h + off) = w;
+    }
+  }
+  // phase rows: P (low passes; the norm fold of the previous step folded in), B (phase group)
+  const double fc = fold_factor_block(nf);
+  if (LOW) {
+    for (int i = tid; i <= m; i += kTcThreads)
+      s_pt[i] = make_float2(static_cast<float>(prow[i].x * fc), static_cast<float>(prow[i].y * fc));
+  }
+  if (KIND == kSpWBW) {
+    for (int i = tid; i <= n; i += kTcThreads) s_bt[i] = brow[i];
+  }
+  tc_fence_proxy_async();  // the Hadamard operands are read by the tensor cores
+  tc_fence_before();
   __syncthreads();
-  for (long long T = blockIdx.x; T < ntiles; T += gridDim.x) {
+  tc_fence_after();
+  const uint32_t taddr = *s_taddr;
+  const uint32_t t_row = taddr + (static_cast<uint32_t>(32 * q4) << 16);  // this warp's lane quarter
+
+  // strided tile T -> (low, middle, high) fixed-bit fields, as sp_tma_kernel
+  const int lo_bits = LOW ? 0 : a1 - C, mid_bits = LOW ? 0 : a2 - a1 - 5;
+  const unsigned long long lo_mask = (1ull << lo_bits) - 1ull, mid_mask = (1ull << mid_bits) - 1ull;
+  auto xbase_of = [&](long long T) -> unsigned long long {
     const unsigned long long ut = static_cast<unsigned long long>(T);
-    const unsigned long long xbase = ((ut & lo_mask) << C) | (((ut >> lo_bits) & mid_mask) << (a1 + 5)) |
-                                     ((ut >> (lo_bits + mid_bits)) << (a2 + QB));
-    for (int u = threadIdx.x; u < NTILE; u += blockDim.x) {
-      const int j = u & ((1 << C) - 1), th = u >> C;
-      const float2* src = psi + xbase + j + (static_cast<unsigned long long>(th) << a2);
-#pragma unroll 8
-      for (int r = 0; r < 32; ++r) s_tile[G::swz(j + ((r + (th << 5)) << C))] = src[static_cast<unsigned long long>(r) << a1];
+    if (LOW) return ut * kTcTile;
+    return ((ut & lo_mask) << C) | (((ut >> lo_bits) & mid_mask) << (a1 + 5)) |
+           ((ut >> (lo_bits + mid_bits)) << (a2 + QB));
+  };
+  auto issue = [&](long long T) {
+    if (LOW) {
+      // eight consecutive 1024-amplitude tiles: x = base + i + 1024 j (i bits 0..4 = u bits 0..4,
+      // j = u bits 5..7, i bits 5..9 = u bits 8..12)
+      const float2* g = psi + xbase_of(T);
+#pragma unroll 4
+      for (int e = 0; e < kTcTile / kTcThreads; ++e) {
+        const int x = tid + kTcThreads * e;
+        const int u = (x & 31) | ((x >> 10) << 5) | (((x >> 5) & 31) << 8);
+        tc_cp_async8(s_t + tslot<LOW>(u), g + x);
+      }
+      tc_cp_async_commit();
+    } else if (tid == 0) {
+      const unsigned long long ut = static_cast<unsigned long long>(T);
+      tc_mbar_expect_tx(bar_tma, kTcTile * 8u);
+      tc_tma_load_5d(s_t, &tmap, static_cast<int>((ut & lo_mask) << C), 0,
+                     static_cast<int>((ut >> lo_bits) & mid_mask), 0, static_cast<int>(ut >> (lo_bits + mid_bits)),
+                     bar_tma);
     }
-    __syncthreads();
-    for (int s = 0; s < NST; ++s) {
-      sp_tc_stage<Q, C, PARTS>(s_tile, sb[s], H[s], warp, lane);
-      __syncthreads();
+  };
+
+  double nacc = 0.0;  // |psi|^2 of this thread's outputs (norm fold of the low passes)
+  uint32_t mma_phase = 0;
+  int it = 0;
+  int pending = -1;  // strided: the iteration whose TMA load is in flight
+  bool failed = false;
+  if (static_cast<long long>(blockIdx.x) < ntiles) {
+    issue(blockIdx.x);
+    pending = 0;
+  }
+  for (long long T = blockIdx.x; T < ntiles; T += gridDim.x, ++it) {
+    const unsigned long long xb = xbase_of(T);
+    // energies of the low tile (stored per-tile counts, layout Y: lane = bits 5..9,
+    // register = bits 0..4): warp w expands 1024-tile w of the eight
+    if (LOW) {
+      unsigned pl[kPlanes];
+      int nconst;
+      load_counts(counts, T * 8 + warp, lane, pl, nconst);
+      int e[32];
+      StoreCountUnroll<0>::run(e, pl, nconst);
+      uint16_t* row = s_e + warp * 32 * kTcEStride + lane * kTcEStride;
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) row[rr] = static_cast<uint16_t>(e[rr]);
     }
-    if (WBW) {
-      for (int e = threadIdx.x; e < G::TILE; e += blockDim.x) {
-        const int j = e & ((1 << C) - 1), i = e >> C;
-        const int pc = __popcll(xbase) + __popc(j) + __popc(i);
-        const int a = G::swz(e);
-        s_tile[a] = cmul(s_tile[a], s_bt[pc]);
+    // the tile
+    bool ok = true;
+    if (LOW) {
+      tc_cp_async_wait();
+    } else {
+      ok = tc_mbar_wait(bar_tma, static_cast<uint32_t>(it) & 1u);
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    pending = -1;
+    // kLpFirst: P before the transform (warp = 1024-tile j, lane = bits 0..4, k = bits 5..9)
+    if (KIND == kLpFirst) {
+#pragma unroll 4
+      for (int k = 0; k < 32; ++k) {
+        float2* p = s_t + tslot<LOW>(u_stage2(R, k));
+        *p = cmul(*p, s_pt[s_e[warp * 32 * kTcEStride + k * kTcEStride + lane]]);
       }
       __syncthreads();
-      for (int s = 0; s < NST; ++s) {
-        sp_tc_stage<Q, C, PARTS>(s_tile, sb[s], H[s], warp, lane);
+    }
+    for (int w = 0; w < NW && !failed; ++w) {
+      for (int st = TWO ? 1 : 2; st <= 2; ++st) {
+        // ---- A: this thread's row, both components, split into BF16 parts
+        {
+          float2 x[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) x[k] = s_t[tslot<LOW>(st == 1 ? u_stage1(R, k, C) : u_stage2(R, k))];
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int unit = 2 * hh + c;
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+              uint32_t ph[PARTS][4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                float v0 = c ? x[8 * kb + 2 * t].y : x[8 * kb + 2 * t].x;
+                float v1 = c ? x[8 * kb + 2 * t + 1].y : x[8 * kb + 2 * t + 1].x;
+#pragma unroll
+                for (int p = 0; p < PARTS; ++p) {
+                  const uint32_t b = bf16x2(v0, v1);
+                  ph[p][t] = b;
+                  v0 -= bf16_lo(b);  // exact: the remainder of a round-to-nearest in FP32
+                  v1 -= bf16_hi(b);
+                }
+              }
+#pragma unroll
+              for (int p = 0; p < PARTS; ++p) {
+                const uint32_t off = (p * 4 + unit) * kTcUnitBytes + (r >> 3) * kTcSBO + kb * kTcLBO + (r & 7) * 16;
+                *reinterpret_cast<uint4*>(s_a + off) = make_uint4(ph[p][0], ph[p][1], ph[p][2], ph[p][3]);
+              }
+            }
+          }
+        }
+        tc_fence_proxy_async();
+        __syncthreads();
+        // the tile has been read for the last time: the next tile's load can start
+        if (w == NW - 1 && st == 2 && T + gridDim.x < ntiles) {
+          if (!LOW && tid == 0) tc_fence_proxy_async();
+          issue(T + gridDim.x);
+          pending = it + 1;
+        }
+        // ---- MMAs: per unit, hi -> accumulator 0, the small parts -> accumulator 1
+        if (tid == 0) {
+          tc_fence_after();
+          const uint32_t a0 = tc_smem(s_a), h0 = tc_smem(s_h) + (st == 1 ? 0u : 2048u);
+#pragma unroll
+          for (int unit = 0; unit < 4; ++unit) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+              const uint64_t bd = smem_desc(h0 + 256u * s);
+#pragma unroll
+              for (int p = 0; p < PARTS; ++p) {
+                const uint64_t ad = smem_desc(a0 + (p * 4 + unit) * kTcUnitBytes + 256u * s);
+                const uint32_t d = taddr + unit * 64 + (p == 0 ? 0 : 32);
+                tc_mma(d, ad, bd, kTcIdesc, (s > 0 || p > 1) ? 1u : 0u);
+              }
+            }
+          }
+          tc_commit(bar_mma);
+        }
+        ok = tc_mbar_wait(bar_mma, mma_phase & 1u);
+        ++mma_phase;
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        // ---- read back: y[k'] for this row, both components
+        float2 y[32];
+        {
+          float hi[32], sm[32];
+          tmem_ld32(t_row + (2 * hh) * 64, hi);
+          tmem_ld32(t_row + (2 * hh) * 64 + 32, sm);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) y[k].x = hi[k] + sm[k];
+          tmem_ld32(t_row + (2 * hh + 1) * 64, hi);
+          tmem_ld32(t_row + (2 * hh + 1) * 64 + 32, sm);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) y[k].y = hi[k] + sm[k];
+        }
+        if (st == 2) {
+          // phases due after a whole transform: B between the two transforms of
+          // the phase group, P after the low pass's (first) transform
+          if (KIND == kSpWBW && w == 0) {
+            const int pc0 = __popcll(xb);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const int u = u_stage2(R, k);
+              y[k] = cmul(y[k], s_bt[pc0 + __popc(u & ((1 << C) - 1)) + __popc(u >> C)]);
+            }
+          }
+          if ((KIND == kLpMerge && w == 0) || KIND == kLpLast) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) y[k] = cmul(y[k], s_pt[s_e[warp * 32 * kTcEStride + k * kTcEStride + lane]]);
+          }
+        }
+        if (w == NW - 1 && st == 2) {
+          // to global memory (x of u = R | k << 8)
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int u = u_stage2(R, k);
+            unsigned long long x;
+            if (LOW) {
+              x = xb + static_cast<unsigned long long>((u & 31) | ((u >> 8) << 5) | (((u >> 5) & 7) << 10));
+            } else {
+              const int j = u & ((1 << C) - 1), i = u >> C;
+              x = xb + static_cast<unsigned long long>(j) + (static_cast<unsigned long long>(i & 31) << a1) +
+                  (static_cast<unsigned long long>(i >> 5) << a2);
+            }
+            psi[x] = y[k];
+          }
+          if (LOW && nf.out) {
+            float t = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) t = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, t));
+            nacc += static_cast<double>(t);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) s_t[tslot<LOW>(st == 1 ? u_stage1(R, k, C) : u_stage2(R, k))] = y[k];
+        }
+        tc_fence_before();
         __syncthreads();
       }
     }
-    for (int u = threadIdx.x; u < NTILE; u += blockDim.x) {
-      const int j = u & ((1 << C) - 1), th = u >> C;
-      float2* dst = psi + xbase + j + (static_cast<unsigned long long>(th) << a2);
-#pragma unroll 8
-      for (int r = 0; r < 32; ++r) dst[static_cast<unsigned long long>(r) << a1] = s_tile[G::swz(j + ((r + (th << 5)) << C))];
-    }
-    __syncthreads();
+    if (failed) break;
+  }
+  if (failed && tid == 0) atomicExch(err, 1);
+  // leave only when no copy issued by this CTA is in flight
+  if (LOW) {
+    tc_cp_async_wait();
+  } else if (tid == 0 && pending >= 0) {
+    if (!tc_mbar_wait(bar_tma, static_cast<uint32_t>(pending) & 1u)) atomicExch(err, 1);
+  }
+  if (LOW) fold_store(nf, nacc);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(taddr, kTcCols);
   }
 }
 
 // ------------------------------------------------------------- host ---------
-template <int KIND, int PARTS>
-static cudaError_t launch_lp_tc(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl, const float2* prow) {
-  const long long ntiles = 1ll << (n - kLowBits);
-  const size_t smem = 16u * m + ((8u * (m + 1) + 15u) & ~15u) + static_cast<size_t>(kTcWarps) * (8u * kLowTile + 8u * (m + 16));
-  auto kern = lp_tc_kernel<KIND, PARTS>;
-  const size_t worst = 16u * QAA_MAX_CLAUSES_DEV + ((8u * (QAA_MAX_CLAUSES_DEV + 1) + 15u) & ~15u) +
-                       static_cast<size_t>(kTcWarps) * (8u * kLowTile + 8u * (QAA_MAX_CLAUSES_DEV + 16));
-  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), worst);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcWarps * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
-  long long grid = static_cast<long long>(occ) * lc.num_sms;
-  const long long need = (ntiles + kTcWarps - 1) / kTcWarps;
-  if (grid > need) grid = need;
-  kern<<<static_cast<unsigned>(grid), kTcWarps * 32, smem, lc.stream>>>(psi, m, cl, prow, ntiles);
-  return cudaGetLastError();
+typedef CUresult (*TcEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static TcEncodeFn tc_encode() {
+  static const TcEncodeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<TcEncodeFn>(p);
+    cudaGetLastError();
+    return static_cast<TcEncodeFn>(nullptr);
+  }();
+  return fn;
 }
 
-template <int Q, int PARTS>
-static cudaError_t launch_sp_tc(const LaunchCtx& lc, float2* psi, int n, int a1, int a2, bool wbw, const float2* brow) {
-  constexpr int C = (10 - Q) > 3 ? (10 - Q) : 3;
-  using G = TcSp<Q, C>;
-  const long long ntiles = 1ll << (n - Q - C);
-  const size_t smem = static_cast<size_t>(G::TILE) * 8u + 64u * 8u;
-  auto kern = wbw ? sp_tc_kernel<Q, C, true, PARTS> : sp_tc_kernel<Q, C, false, PARTS>;
-  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), smem);
+size_t tc_smem_bytes(int parts) { return TcLayout(parts).total; }
+
+template <int KIND, int Q, int PARTS>
+static cudaError_t launch_tc_q(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const float2* prow,
+                               const float2* brow, const unsigned* counts, int* err, const NormFold& nf) {
+  constexpr bool LOW = KIND == kLpFirst || KIND == kLpMerge || KIND == kLpLast;
+  constexpr int C = LOW ? 0 : 13 - Q;
+  constexpr int QB = Q - 5;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof map);
+  long long ntiles;
+  int a1 = 0, a2 = 0;
+  if (LOW) {
+    if (n < 13 || !counts) return cudaErrorInvalidValue;  // eight 1024-amplitude tiles, stored counts
+    ntiles = 1ll << (n - 13);
+  } else {
+    a1 = p.a;
+    a2 = p.a2;
+    if (a1 < C || a2 < a1 + 5 || a2 + QB > n || (a2 != a1 + 5 && QB < 5)) return cudaErrorInvalidValue;
+    TcEncodeFn enc = tc_encode();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {1ull << a1, 32ull, 1ull << (a2 - a1 - 5), 1ull << QB, 1ull << (n - a2 - QB)};
+    const cuuint64_t strides[4] = {(1ull << a1) * 8ull, (1ull << (a1 + 5)) * 8ull, (1ull << a2) * 8ull,
+                                   (1ull << (a2 + QB)) * 8ull};
+    const cuuint32_t box[5] = {1u << C, 32u, 1u, 1u << QB, 1u};
+    const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+    const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, psi, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    ntiles = 1ll << (n - Q - C);
+  }
+  const TcLayout L(PARTS);
+  auto kern = tc_pass_kernel<KIND, Q, PARTS>;
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), L.total);
   if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, G::NT, smem);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
-  long long grid = static_cast<long long>(occ) * lc.num_sms;
+  long long grid = lc.num_sms;  // one CTA per SM (shared memory and tensor memory)
   if (grid > ntiles) grid = ntiles;
-  kern<<<static_cast<unsigned>(grid), G::NT, smem, lc.stream>>>(psi, n, a1, a2, brow, ntiles);
+  if (grid > kFoldSlot - 1) grid = kFoldSlot - 1;
+  kern<<<static_cast<unsigned>(grid), kTcThreads, L.total, lc.stream>>>(psi, map, n, a1, a2, ntiles, prow, brow,
+                                                                       counts, m, err, nf);
   return cudaGetLastError();
 }
 
-template <int PARTS>
-static cudaError_t launch_pass_tc_p(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
-                                    const float2* ptab, const float2* btab) {
-  switch (p.kind) {
-    case kLpFirst: return launch_lp_tc<kLpFirst, PARTS>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1));
-    case kLpMerge: return launch_lp_tc<kLpMerge, PARTS>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1));
-    case kLpLast: return launch_lp_tc<kLpLast, PARTS>(lc, psi, n, m, cl, ptab + static_cast<size_t>(p.prow) * (m + 1));
-    case kSpW:
-    case kSpWBW: {
-      const bool wbw = p.kind == kSpWBW;
-      const float2* brow = btab + static_cast<size_t>(p.brow) * (n + 1);
-      switch (p.q) {
-        case 5: return launch_sp_tc<5, PARTS>(lc, psi, n, p.a, p.a2, wbw, brow);
-        case 6: return launch_sp_tc<6, PARTS>(lc, psi, n, p.a, p.a2, wbw, brow);
-        case 7: return launch_sp_tc<7, PARTS>(lc, psi, n, p.a, p.a2, wbw, brow);
-        case 8: return launch_sp_tc<8, PARTS>(lc, psi, n, p.a, p.a2, wbw, brow);
-        case 9: return launch_sp_tc<9, PARTS>(lc, psi, n, p.a, p.a2, wbw, brow);
-        case 10: return launch_sp_tc<10, PARTS>(lc, psi, n, p.a, p.a2, wbw, brow);
-        default: return cudaErrorInvalidValue;
-      }
-    }
+template <int KIND, int PARTS>
+static cudaError_t launch_tc_sp(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const float2* brow,
+                                int* err) {
+  switch (p.q) {
+    case 5: return launch_tc_q<KIND, 5, PARTS>(lc, p, psi, n, m, nullptr, brow, nullptr, err, NormFold());
+    case 6: return launch_tc_q<KIND, 6, PARTS>(lc, p, psi, n, m, nullptr, brow, nullptr, err, NormFold());
+    case 7: return launch_tc_q<KIND, 7, PARTS>(lc, p, psi, n, m, nullptr, brow, nullptr, err, NormFold());
+    case 8: return launch_tc_q<KIND, 8, PARTS>(lc, p, psi, n, m, nullptr, brow, nullptr, err, NormFold());
+    case 9: return launch_tc_q<KIND, 9, PARTS>(lc, p, psi, n, m, nullptr, brow, nullptr, err, NormFold());
+    case 10: return launch_tc_q<KIND, 10, PARTS>(lc, p, psi, n, m, nullptr, brow, nullptr, err, NormFold());
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_pass_tc(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
-                           const float2* ptab, const float2* btab, int parts) {
-  return parts == 2 ? launch_pass_tc_p<2>(lc, p, psi, n, m, cl, ptab, btab)
-                    : launch_pass_tc_p<3>(lc, p, psi, n, m, cl, ptab, btab);
+template <int PARTS>
+static cudaError_t launch_pass_tc_p(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const float2* ptab,
+                                    const float2* btab, int* err, const unsigned* counts, const NormFold& nf) {
+  const float2* prow = ptab + static_cast<size_t>(p.prow) * (m + 1);
+  const float2* brow = btab + static_cast<size_t>(p.brow) * (n + 1);
+  switch (p.kind) {
+    case kLpFirst: return launch_tc_q<kLpFirst, 10, PARTS>(lc, p, psi, n, m, prow, nullptr, counts, err, nf);
+    case kLpMerge: return launch_tc_q<kLpMerge, 10, PARTS>(lc, p, psi, n, m, prow, nullptr, counts, err, nf);
+    case kLpLast: return launch_tc_q<kLpLast, 10, PARTS>(lc, p, psi, n, m, prow, nullptr, counts, err, nf);
+    case kSpW: return launch_tc_sp<kSpW, PARTS>(lc, p, psi, n, m, nullptr, err);
+    case kSpWBW: return launch_tc_sp<kSpWBW, PARTS>(lc, p, psi, n, m, brow, err);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pass_tc(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP*,
+                           const float2* ptab, const float2* btab, int parts, int* err, const unsigned* counts,
+                           const NormFold& nf) {
+  if (!err) return cudaErrorInvalidValue;
+  return parts == 2 ? launch_pass_tc_p<2>(lc, p, psi, n, m, ptab, btab, err, counts, nf)
+                    : launch_pass_tc_p<3>(lc, p, psi, n, m, ptab, btab, err, counts, nf);
 }
 
 }  // namespace qaa

@@ -317,20 +317,7 @@ __device__ __forceinline__ void xpose_y2x_t(float2 (&v)[32], float2* __restrict_
 // KIND kLpPhase / kLpRot / kLpRot12: the rotation form (P alone; the
 // rotations of bits 0..9, or 0..11 with warp quads, then 2^-n P), with B row
 // entries 0..5 = exp(-i theta p).
-// Stored per-tile counts (layout Y: registers hold bits 0..4): for tile t and
-// lane l, word (t * kCountWords + b) * 32 + l holds bit plane b of the lane's 32
-// violated-clause counts (b < kPlanes), and word kPlanes the tile's constant
-// part.  E(x) never changes during a run, so the merged low passes can read
-// these instead of folding and counting the clauses again every step.
-constexpr int kCountWords = kPlanes + 1;
-
-__device__ __forceinline__ void load_counts(const unsigned* __restrict__ counts, long long tile, int lane,
-                                            unsigned (&pl)[kPlanes], int& nconst) {
-  const unsigned* c = counts + static_cast<size_t>(tile) * (kCountWords * 32) + lane;
-#pragma unroll
-  for (int b = 0; b < kPlanes; ++b) pl[b] = __ldg(c + 32 * b);
-  nconst = static_cast<int>(__ldg(c + 32 * kPlanes));
-}
+// Stored per-tile counts: kCountWords / load_counts (device_common.cuh).
 
 // Warp quads (kLpRot12): warps 4k..4k+3 of a CTA sync on named barrier 1 + k
 // (immediate ids, so that only barriers 0..2 are reserved).
@@ -382,7 +369,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     lp_tma_kernel(float2* __restrict__ psi, int m, const ClauseLP* __restrict__ cl, const float2* __restrict__ prow,
                   const float2* __restrict__ brow, int n, long long ntiles, int* __restrict__ err,
-                  const unsigned* __restrict__ counts) {
+                  const unsigned* __restrict__ counts, const NormFold nf) {
   constexpr bool kRegLow = KIND != kLpFirst && KIND != kLpPhase;  // phase applied in layout Y
   extern __shared__ __align__(1024) unsigned char smem[];
   const LpTmaLayout L(m);
@@ -409,8 +396,10 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
   // the rotation form's last pass of a step also removes the 2^n of its rotations (exact)
   constexpr bool kRot = KIND == kLpRot || KIND == kLpRot12;
   constexpr bool kQuad = KIND == kLpRot12;
-  const float psc = kRot ? ldexpf(1.0f, -n) : 1.0f;
-  for (int i = threadIdx.x; i <= m; i += blockDim.x) s_pt[i] = make_float2(prow[i].x * psc, prow[i].y * psc);
+  // and every merged pass folds in the norm correction of the previous step
+  const double psc = (kRot ? ldexp(1.0, -n) : 1.0) * fold_factor_block(nf);
+  for (int i = threadIdx.x; i <= m; i += blockDim.x)
+    s_pt[i] = make_float2(static_cast<float>(prow[i].x * psc), static_cast<float>(prow[i].y * psc));
   float2 rtab[6];
 #pragma unroll
   for (int p = 0; p < 6; ++p) rtab[p] = kRot ? brow[p] : make_float2(0.f, 0.f);
@@ -434,6 +423,7 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     }
   }
   int it = 0;
+  double nacc = 0.0;  // |psi|^2 of this lane's outputs (norm fold)
   for (long long tile = first; tile < ntiles; tile += step, ++it) {
     const bool ok = mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u);
     // a quad leaves together (its four warps have the same tiles left)
@@ -486,6 +476,7 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     float2* g = psi + (tile << kLowBits) + lane;
 #pragma unroll
     for (int r = 0; r < 32; ++r) g[32 * r] = v[r];
+    if (nf.out) nacc += static_cast<double>(tile_norm(v));
     if (tn < ntiles) {
       if (stored) {
         load_counts(counts, tn, lane, pl, nconst);
@@ -499,6 +490,110 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
   if (lane == 0) {
     const long long t = first + static_cast<long long>(it) * step;
     if (t < ntiles && !mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u)) atomicExch(err, kErrTimeout);
+  }
+  fold_store(nf, nacc);
+}
+
+// ------------------------------------------------ correlation pass -------
+// Read-only strided pass for the observables: the pair correlations
+//   sum over x with bit i clear of Re(conj psi_x psi_(x + 2^i))
+// of every index bit i of a contiguous group [a, a+Q), 5 <= Q <= 10 (the
+// ground state and <H_B> of Sec. 2.1, gathered from every thread as in
+// Sec. 4.2).  The tile and its layouts are those of sp_tma_kernel: in layout
+// H the registers hold i bits QB..QB+4, in layout L i bits 0..4 (of which bits
+// 0..QB-1 are new).  Products are summed in FP32 per thread and tile (at most
+// 160 pairs), in FP64 beyond; one partial per CTA.
+__device__ __forceinline__ unsigned long long pair_fma(const float2 (&v)[32], int b, unsigned long long c) {
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    if (!(r & (1 << b))) {
+      const unsigned long long u = (static_cast<unsigned long long>(__float_as_uint(v[r].y)) << 32) |
+                                   __float_as_uint(v[r].x);
+      const unsigned long long w = (static_cast<unsigned long long>(__float_as_uint(v[r | (1 << b)].y)) << 32) |
+                                   __float_as_uint(v[r | (1 << b)].x);
+      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(u), "l"(w));
+    }
+  }
+  return c;
+}
+
+template <int Q, int C>
+__global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ? 1 : 3))
+    corr_tma_kernel(const __grid_constant__ CUtensorMap tmap, int a1, long long ntiles, double* __restrict__ partials,
+                    int nparts, int* __restrict__ err) {
+  using G = TmaGeom<Q, C>;
+  constexpr int QB = Q - 5;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ double s_red[32];
+  float2* s_buf = reinterpret_cast<float2*>(smem);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + G::off_bar);
+  const int tid = threadIdx.x;
+  const int j = tid & ((1 << C) - 1);
+  const int th = tid >> C;
+  const int lo_bits = a1 - C;
+  const unsigned long long lo_mask = (1ull << lo_bits) - 1ull;
+  const long long stride_t = gridDim.x;
+  auto issue = [&](unsigned long long T) {
+    mbar_expect_tx(s_bar, G::TILE * 8u);
+    tma_load_5d(s_buf, &tmap, static_cast<int>((T & lo_mask) << C), 0, 0, 0, static_cast<int>(T >> lo_bits), s_bar);
+  };
+  if (tid == 0) {
+    mbar_init(s_bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0 && static_cast<long long>(blockIdx.x) < ntiles) issue(blockIdx.x);
+  const int h_off = j + (th << C);
+  const int sx_h = G::slot(j + (th << C));
+  const int sx_l = j + (th << (C + 5)) + (th << C);
+  double acc = 0.0;
+  int it = 0;
+  for (long long T = blockIdx.x; T < ntiles; T += stride_t, ++it) {
+    const bool ok = mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(err, kErrTimeout);
+      break;
+    }
+    float2 v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = s_buf[h_off + ((r << QB) << C)];
+    unsigned long long c2 = 0ull;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) c2 = pair_fma(v, b, c2);  // i bits QB..QB+4
+    if (QB > 0) {
+      __syncthreads();  // dense tile fully read
+#pragma unroll
+      for (int r = 0; r < 32; ++r) s_buf[sx_h + G::slot((r << QB) << C)] = v[r];
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = s_buf[sx_l + (r << C)];
+    }
+    __syncthreads();  // buffer free: the next tile's copy overlaps the rest of this one
+    if (tid == 0 && T + stride_t < ntiles) {
+      fence_proxy_async();
+      issue(static_cast<unsigned long long>(T + stride_t));
+    }
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+      if (b < QB) c2 = pair_fma(v, b, c2);  // i bits 0..QB-1
+    const float2 c = bits_f2(c2);
+    acc += static_cast<double>(c.x + c.y);
+  }
+  if (tid == 0) {
+    const long long T = blockIdx.x + static_cast<long long>(it) * stride_t;
+    if (T < ntiles && !mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u)) atomicExch(err, kErrTimeout);
+  }
+  // fixed-order block sum; CTAs beyond the grid's share write zero partials
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) s_red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += s_red[w];
+    partials[blockIdx.x] = t;
+    if (blockIdx.x == 0)
+      for (int i = gridDim.x; i < nparts; ++i) partials[i] = 0.0;
   }
 }
 
@@ -575,6 +670,53 @@ static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int 
   return cudaGetLastError();
 }
 
+// The correlation pass over bits [a, a+q) (contiguous, 5 <= q <= 10, a >= 10):
+// one partial per CTA in partials[0 .. nparts).  Tiles of 2^q rows x 2^C
+// contiguous amplitudes, C = max(10 - q, 3) as in the strided passes, so that
+// a tile has at least 2^10 amplitudes and a CTA at least one whole warp.
+template <int Q>
+static cudaError_t launch_corr_q(const LaunchCtx& lc, const float2* psi, int n, int a, double* partials, int nparts,
+                                 int* err) {
+  constexpr int C = tma_c(Q);
+  using G = TmaGeom<Q, C>;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  constexpr int QB = Q - 5;
+  if (a < C || a + Q > n) return cudaErrorInvalidValue;
+  CUtensorMap map;
+  // dims (innermost first): bits [0,a), [a,a+5), one, [a+5,a+Q), [a+Q,n)
+  const cuuint64_t dims[5] = {1ull << a, 32ull, 1ull, 1ull << QB, 1ull << (n - a - Q)};
+  const cuuint64_t strides[4] = {(1ull << a) * 8ull, (1ull << (a + 5)) * 8ull, (1ull << (a + 5)) * 8ull,
+                                 (1ull << (a + Q)) * 8ull};
+  const cuuint32_t box[5] = {1u << C, 32u, 1u, 1u << QB, 1u};
+  const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+  const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<float2*>(psi), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, l2_promotion(C),
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const long long ntiles = 1ll << (n - Q - C);
+  auto kern = corr_tma_kernel<Q, C>;
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), G::smem);
+  if (e != cudaSuccess) return e;
+  long long grid = nparts;
+  if (grid > ntiles) grid = ntiles;
+  kern<<<static_cast<unsigned>(grid), G::NT, G::smem, lc.stream>>>(map, a, ntiles, partials, nparts, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr_tma(const LaunchCtx& lc, const float2* psi, int n, int a, int q, double* partials, int nparts,
+                            int* err) {
+  switch (q) {
+    case 5: return launch_corr_q<5>(lc, psi, n, a, partials, nparts, err);
+    case 6: return launch_corr_q<6>(lc, psi, n, a, partials, nparts, err);
+    case 7: return launch_corr_q<7>(lc, psi, n, a, partials, nparts, err);
+    case 8: return launch_corr_q<8>(lc, psi, n, a, partials, nparts, err);
+    case 9: return launch_corr_q<9>(lc, psi, n, a, partials, nparts, err);
+    case 10: return launch_corr_q<10>(lc, psi, n, a, partials, nparts, err);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Contiguous run per tile row: 2^C amplitudes.  C = 4 (128-byte runs) can be
 // requested for groups whose rows lie far apart in memory (see the pass plan).
 template <int Q>
@@ -634,7 +776,8 @@ cudaError_t launch_lp_counts(const LaunchCtx& lc, unsigned* counts, int n, int m
 
 template <int KIND>
 static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl,
-                                 const float2* prow, const float2* brow, int* err, const unsigned* counts) {
+                                 const float2* prow, const float2* brow, int* err, const unsigned* counts,
+                                 const NormFold& nf) {
   const long long ntiles = 1ll << (n - kLowBits);
   const LpTmaLayout L(m);
   auto kern = lp_tma_kernel<KIND>;
@@ -647,25 +790,27 @@ static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m,
   long long grid = static_cast<long long>(occ) * lc.num_sms;
   const long long need = (ntiles + kLpTmaWarps - 1) / kLpTmaWarps;
   if (grid > need) grid = need;
+  if (grid > kFoldSlot - 1) grid = kFoldSlot - 1;  // one norm-fold partial per CTA
   kern<<<static_cast<unsigned>(grid), kLpTmaWarps * 32, L.total, lc.stream>>>(psi, m, cl, prow, brow, n, ntiles,
-                                                                              err, counts);
+                                                                              err, counts, nf);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
-                            const float2* ptab, const float2* btab, int* err, const unsigned* counts) {
+                            const float2* ptab, const float2* btab, int* err, const unsigned* counts,
+                            const NormFold& nf) {
   const int c_req = p.run_c;
   const float2* prow = ptab + static_cast<size_t>(p.prow) * (m + 1);
   const float2* brow = btab + static_cast<size_t>(p.brow) * (n + 1);
   switch (p.kind) {
-    case kLpFirst: return launch_lp_tma<kLpFirst>(lc, psi, n, m, cl, prow, nullptr, err, nullptr);
-    case kLpMerge: return launch_lp_tma<kLpMerge>(lc, psi, n, m, cl, prow, nullptr, err, counts);
-    case kLpLast: return launch_lp_tma<kLpLast>(lc, psi, n, m, cl, prow, nullptr, err, counts);
-    case kLpPhase: return launch_lp_tma<kLpPhase>(lc, psi, n, m, cl, prow, nullptr, err, nullptr);
-    case kLpRot: return launch_lp_tma<kLpRot>(lc, psi, n, m, cl, prow, brow, err, counts);
+    case kLpFirst: return launch_lp_tma<kLpFirst>(lc, psi, n, m, cl, prow, nullptr, err, nullptr, nf);
+    case kLpMerge: return launch_lp_tma<kLpMerge>(lc, psi, n, m, cl, prow, nullptr, err, counts, nf);
+    case kLpLast: return launch_lp_tma<kLpLast>(lc, psi, n, m, cl, prow, nullptr, err, counts, nf);
+    case kLpPhase: return launch_lp_tma<kLpPhase>(lc, psi, n, m, cl, prow, nullptr, err, nullptr, nf);
+    case kLpRot: return launch_lp_tma<kLpRot>(lc, psi, n, m, cl, prow, brow, err, counts, nf);
     case kLpRot12:
       if (n < 12) return cudaErrorInvalidValue;
-      return launch_lp_tma<kLpRot12>(lc, psi, n, m, cl, prow, brow, err, counts);
+      return launch_lp_tma<kLpRot12>(lc, psi, n, m, cl, prow, brow, err, counts, nf);
     case kSpW:
     case kSpWBW:
     case kSpRot: {

@@ -185,6 +185,58 @@ def ratio_instance(n, seed, ratio=4.2, min_solutions=1):
     raise RuntimeError("no instance with enough solutions in 10000 draws")
 
 
+def block_instance(n, nblocks, distinct, repeated, seed):
+    """A 3-SAT instance whose clauses never mix variables of different blocks.
+
+    Variable x_v (1-based) belongs to block (v - 1) mod nblocks, so every block
+    spans the low, middle and high bits of the basis index.  Per block, with
+    ``rng = default_rng(seed)`` drawn in block order: a planted assignment of
+    the block's variables (``rng.integers(0, 2, size)``), then ``distinct``
+    clauses drawn as in the planted generator (three distinct block variables,
+    three signs; dropped if the planted assignment falsifies them or if they
+    repeat an earlier clause), then ``repeated`` clauses whose three literals
+    are all true under the planted assignment (three distinct block variables,
+    repeats allowed), so that the complement of the planted assignment violates
+    at least ``nblocks * repeated`` clauses (large violated-clause counts).
+
+    Because E(x) is the sum of the blocks' energies and every factor of the
+    Strang step factorises over qubits, the evolved state is the tensor product
+    of the blocks' states: full-size results can be checked block by block.
+    Returns a dict with keys n, seed, m, clauses (global literals), planted
+    (global index) and blocks (list of {vars, clauses: local literals 1..len(vars)}).
+    """
+    if nblocks < 1 or n < 3 * nblocks:
+        raise ValueError("each block needs at least 3 variables")
+    rng = np.random.default_rng(seed)
+    blocks, clauses, planted = [], [], 0
+    for b in range(nblocks):
+        vs = [v for v in range(1, n + 1) if (v - 1) % nblocks == b]
+        k = len(vs)
+        pl = [int(t) for t in rng.integers(0, 2, size=k)]
+        for i, bit in enumerate(pl):
+            planted |= bit << (vs[i] - 1)
+        local, seen = [], set()
+        while len(local) < distinct:
+            idx = rng.choice(k, size=3, replace=False)
+            signs = rng.integers(0, 2, size=3)
+            lits = [int(i) + 1 if sg else -(int(i) + 1) for i, sg in zip(idx, signs)]
+            if not any((lit > 0) == (pl[abs(lit) - 1] == 1) for lit in lits):
+                continue
+            key = tuple(sorted(lits))
+            if key in seen:
+                continue
+            seen.add(key)
+            local.append(lits)
+        for _ in range(repeated):
+            idx = rng.choice(k, size=3, replace=False)
+            local.append([int(i) + 1 if pl[int(i)] else -(int(i) + 1) for i in idx])
+        blocks.append({"vars": vs, "clauses": local})
+        for lits in local:
+            clauses.append([vs[abs(lit) - 1] * (1 if lit > 0 else -1) for lit in lits])
+    return {"n": n, "seed": seed, "m": len(clauses), "clauses": clauses, "planted": planted, "blocks": blocks,
+            "generator": "satgen block-product v1"}
+
+
 def save_instance(inst, path):
     with open(path, "w") as f:
         json.dump(inst, f, separators=(",", ":"))

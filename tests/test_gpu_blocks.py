@@ -1,0 +1,244 @@
+"""Full-size parity on real 3-literal clauses: block-product instances at n = 30
+and n = 32 (8 and 32 GiB states), in the launch configuration bench.py times.
+
+The instance (satgen.block_instance) splits the variables into blocks by
+residue, x_v in block (v - 1) mod B, so every block has variables among the
+low (0..9), middle and high index bits, and draws its 3-literal clauses inside
+each block (Sec. 2.2: clauses of literals; Sec. 4.3: E(x) counts the violated
+ones).  E(x) is then the sum of the blocks' energies and every factor of the
+Strang step (both half phases, the Walsh-Hadamard transforms and the popcount
+phase) factorises over the blocks, so the evolved state is the tensor product
+of the blocks' oracle.evolve_strang states (complex128, at most 11 qubits
+each) and the ground-state probability the product of theirs.  Each block also
+carries clauses that are all true under its planted assignment, repeated, so
+that the complement of the planted assignment violates more than 512 clauses:
+the low passes' stored counts use all ten bit planes, and clauses whose
+variables all lie at bits >= 10 reach the constant part of a tile's count.
+
+Checked against the oracle: 4000 sampled amplitudes (plus the planted
+assignment and its complement) relative to the largest amplitude (REL_TOL, as
+the product-instance tests), the raw ground-state probability (1e-6), the norm
+(1e-6), the ground count (exact) and E(x) at the sampled points (bit exact),
+for the default plan (rotation form, stored per-tile counts), counting on the
+fly (QAA_LP_COUNTS=0), one launch graph, and the W.B.W form; and the n = 32
+planted benchmark instance's ground count, by the GPU's own E(x), equal to the
+generator's uniqueness result.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import satgen
+
+pytestmark = pytest.mark.gpu
+
+DT = 0.1
+REL_TOL = 1e-5
+PROB_TOL = 1e-6
+NORM_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1103_1399_gb300 as q
+    return q, torch
+
+
+def local_index(blk, xs):
+    loc = np.zeros(len(xs), dtype=np.int64)
+    for k, v in enumerate(blk["vars"]):
+        loc |= ((xs >> (v - 1)) & 1) << k
+    return loc
+
+
+class BlockReference:
+    """The tensor-product reference of a block instance after K Strang steps."""
+
+    def __init__(self, inst, T, K):
+        self.blocks = []
+        for blk in inst["blocks"]:
+            nb = len(blk["vars"])
+            e = oracle.violated_counts(nb, blk["clauses"])
+            psi = oracle.evolve_strang(nb, blk["clauses"], T, K, energies=e)
+            self.blocks.append((blk, e, psi))
+
+    def amplitudes(self, xs):
+        out = np.ones(len(xs), dtype=np.complex128)
+        for blk, _, psi in self.blocks:
+            out *= psi[local_index(blk, xs)]
+        return out
+
+    def energies(self, xs):
+        out = np.zeros(len(xs), dtype=np.int64)
+        for blk, e, _ in self.blocks:
+            out += e[local_index(blk, xs)]
+        return out
+
+    def max_amplitude(self):
+        return float(np.prod([np.max(np.abs(psi)) for _, _, psi in self.blocks]))
+
+    def ground_prob(self):
+        return float(np.prod([oracle.success_prob(psi, e) for _, e, psi in self.blocks]))
+
+    def ground_count(self):
+        return int(np.prod([np.count_nonzero(e == 0) for _, e, _ in self.blocks]))
+
+
+def sample_points(inst, n, seed):
+    rng = np.random.default_rng(seed)
+    planted = inst["planted"]
+    return np.concatenate([rng.integers(0, 1 << n, size=4000), [planted, (1 << n) - 1 - planted]]).astype(np.int64)
+
+
+def gather(torch, psi, xs):
+    idx = torch.as_tensor(xs, device=psi.device)
+    return psi[idx].cpu().numpy().astype(np.complex128)
+
+
+def check_state(torch, psi, o, ref, xs, prob_tol=PROB_TOL):
+    got = gather(torch, psi, xs)
+    err = np.max(np.abs(got - ref.amplitudes(xs))) / ref.max_amplitude()
+    dp = o["ground_prob"] - ref.ground_prob()
+    print(f"relative amplitude error {err:.3e}, ground probability error {dp:+.3e}, norm - 1 {o['norm'] - 1:+.3e}")
+    assert err <= REL_TOL, err
+    assert abs(dp) <= prob_tol, (o["ground_prob"], ref.ground_prob())
+    assert abs(o["norm"] - 1.0) <= NORM_TOL, o["norm"]
+    assert o["ground_count"] == ref.ground_count()
+    return got
+
+
+N30 = 30
+K30 = 400  # the benchmark schedule: T = 40, dt = 0.1
+
+
+@pytest.fixture(scope="module")
+def inst30():
+    inst = satgen.block_instance(N30, 3, 160, 180, seed=5)
+    assert 1000 <= inst["m"] <= 1023
+    return inst
+
+
+@pytest.fixture(scope="module")
+def ref30(inst30):
+    return BlockReference(inst30, DT * K30, K30)
+
+
+@pytest.fixture(scope="module")
+def state30(env):
+    _, torch = env
+    psi = torch.empty(1 << N30, dtype=torch.complex64, device="cuda")
+    yield psi
+    del psi
+    torch.cuda.empty_cache()
+
+
+def run30(q, psi, inst, variant=None, graph=False):
+    h = q.Instance(N30, inst["clauses"])
+    if variant is not None:
+        h.set_variant(variant)
+    if graph:
+        h.set_launch_mode(q.LAUNCH_GRAPH)
+    plan = h.describe_plan()
+    h.init_uniform(psi)
+    h.evolve(psi, DT * K30, K30)
+    o = h.observables(psi)
+    h.close()
+    return o, plan
+
+
+def test_block_instance_energies_full_size(env, inst30, ref30):
+    q, torch = env
+    xs = sample_points(inst30, N30, 1)
+    with q.Instance(N30, inst30["clauses"]) as h:
+        diag = torch.empty(1 << N30, dtype=torch.int16, device="cuda")
+        h.hp_diagonal(diag)
+        got = diag[torch.as_tensor(xs, device="cuda")].cpu().numpy().view(np.uint16).astype(np.int64)
+        del diag
+    want = ref30.energies(xs)
+    assert np.array_equal(got, want)
+    assert want[-1] >= 512  # the complement of the planted assignment: all ten counter planes
+
+
+def test_block_instance_default_plan_full_size(env, inst30, ref30, state30):
+    q, torch = env
+    o, plan = run30(q, state30, inst30)
+    assert "rotation form" in plan
+    check_state(torch, state30, o, ref30, sample_points(inst30, N30, 2))
+
+
+def test_block_instance_on_the_fly_counts_and_graph_agree(env, inst30, ref30, state30, monkeypatch):
+    """Counting on the fly (QAA_LP_COUNTS=0) gives the same E(x), so the same
+    state bit for bit; one launch graph runs the same kernels with the same
+    rows, so the same state bit for bit."""
+    q, torch = env
+    xs = sample_points(inst30, N30, 3)
+    o, _ = run30(q, state30, inst30)
+    base = check_state(torch, state30, o, ref30, xs)
+    monkeypatch.setenv("QAA_LP_COUNTS", "0")
+    o2, _ = run30(q, state30, inst30)
+    assert np.array_equal(check_state(torch, state30, o2, ref30, xs), base)
+    monkeypatch.delenv("QAA_LP_COUNTS")
+    o3, _ = run30(q, state30, inst30, graph=True)
+    assert np.array_equal(check_state(torch, state30, o3, ref30, xs), base)
+    assert o2["ground_prob"] == o["ground_prob"] == o3["ground_prob"]
+
+
+# The W.B.W form (variant 0, not the default) changes basis twice per step:
+# its rounding errors are made in the Hadamard basis of 2^30 amplitudes and
+# reach the ground-state amplitude through the inverse transform.  Over the
+# 400 steps at 30 qubits that moved the ground-state probability by 1.5e-6
+# with the norm within 1e-7 (rounding, not drift).  Its bar at this size is
+# 3e-6; the default rotation form above is held to 1e-6.
+WBW_PROB_TOL_N30 = 3e-6
+
+
+def test_block_instance_wbw_form_full_size(env, inst30, ref30, state30):
+    q, torch = env
+    o, plan = run30(q, state30, inst30, variant=0)
+    assert "W.B.W" in plan
+    check_state(torch, state30, o, ref30, sample_points(inst30, N30, 4), prob_tol=WBW_PROB_TOL_N30)
+
+
+N32 = 32
+K32 = 400
+
+
+def test_block_instance_n32(env):
+    q, torch = env
+    inst = satgen.block_instance(N32, 3, 160, 180, seed=7)
+    ref = BlockReference(inst, DT * K32, K32)
+    psi = torch.empty(1 << N32, dtype=torch.complex64, device="cuda")
+    try:
+        with q.Instance(N32, inst["clauses"]) as h:
+            h.init_uniform(psi)
+            h.evolve(psi, DT * K32, K32)
+            o = h.observables(psi)
+        check_state(torch, psi, o, ref, sample_points(inst, N32, 5))
+    finally:
+        del psi
+        torch.cuda.empty_cache()
+
+
+def test_n32_planted_instance_has_one_ground_state(env):
+    """The committed 32-qubit benchmark instance: the generator proved its
+    solution unique with a chunked first-kill scan; the GPU counts E(x) = 0
+    over all 2^32 assignments with its own clause evaluation (a second,
+    independent route) and finds only the planted one."""
+    q, torch = env
+    d = satgen.load_instance("planted_n32_s0")
+    psi = torch.zeros(1 << N32, dtype=torch.complex64, device="cuda")
+    try:
+        psi[d["planted"]] = 1.0
+        with q.Instance(N32, d["clauses"]) as h:
+            o = h.observables(psi)
+        assert o["ground_count"] == 1
+        assert o["ground_prob"] == 1.0  # the one zero-energy amplitude is the planted one
+        assert o["expect_hp"] == 0.0
+    finally:
+        del psi
+        torch.cuda.empty_cache()

@@ -1,8 +1,9 @@
 """The 20-qubit configuration's long schedules (T = 40 and T = 160 at dt = 0.05:
 800 and 3200 Strang steps) against stored complex128 oracle results
 (tests/golden/n20_T*.json, written by tests/golden/make_n20_long.py, which
-calls only the oracle).  Checked: the normalised ground-state probability
-(1e-6), <H_P> and <H_B> (1e-4 absolute), the norm drift (5e-6 per 400 steps)
+calls only the oracle).  Checked: the ground-state probability as returned and
+normalised (1e-6 each), <H_P> and <H_B> (1e-4 absolute), the norm (1e-6: the
+low passes fold it back every step)
 and the amplitudes at 257 stored indices, the planted solution among them
 (1e-5 absolute, the FP32 bar)."""
 
@@ -44,8 +45,9 @@ def test_n20_long_schedule_matches_stored_oracle(env, T, variant):
     got = psi[idx].cpu().numpy().astype(np.complex128)
     ref = np.array([complex(a, b) for a, b in g["amplitudes"]])
     assert np.max(np.abs(got - ref)) <= 1e-5
+    assert abs(o["ground_prob"] - g["success_prob"]) <= 1e-6
     assert abs(o["ground_prob"] / o["norm"] - g["success_prob"]) <= 1e-6
-    assert abs(o["norm"] - 1.0) <= 5e-6 * (K / 400)
+    assert abs(o["norm"] - 1.0) <= 1e-6
     assert abs(o["expect_hp"] - g["expect_hp"]) <= 1e-4
     assert abs(o["expect_hb"] - g["expect_hb"]) <= 1e-4
     assert o["ground_count"] == 1
@@ -65,7 +67,7 @@ def test_n20_adiabatic_trend(env):
             inst.init_uniform(psi)
             inst.evolve(psi, float(T), int(round(T / 0.05)))
             o = inst.observables(psi)
-            probs[T] = o["ground_prob"] / o["norm"]
+            probs[T] = o["ground_prob"]
     assert probs[10] < probs[40] < probs[160]
     assert probs[160] > 0.9
     for T in (40, 160):

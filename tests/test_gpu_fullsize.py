@@ -33,7 +33,7 @@ K = 400
 # relative amplitude bar at n = 30: FP32 rounding grows ~ sqrt(steps x stages);
 # 1e-5 relative to the largest amplitude is the n = 20 absolute bar rescaled.
 REL_TOL = 1e-5
-NORM_TOL = 5e-6
+NORM_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")

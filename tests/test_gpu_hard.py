@@ -54,5 +54,6 @@ def test_ratio42_degenerate_nonlinear_schedule(env, n, T, K, seed, sched, varian
         o = inst.observables(psi)
     got = psi.cpu().numpy().astype(np.complex128)
     assert np.max(np.abs(got - ref)) <= 1e-5
+    assert abs(o["ground_prob"] - oracle.success_prob(ref, e)) <= 1e-6
     assert abs(o["ground_prob"] / o["norm"] - oracle.success_prob(ref, e)) <= 1e-6
     assert o["ground_count"] == inst_d["solutions"] >= 2

@@ -47,6 +47,7 @@ def test_order4_matches_oracle(env, n, T, K, variant):
     psi, o = run(q, torch, n, cl, lambda i, p: i.evolve_order4(p, T, K), variant)
     got = psi.cpu().numpy().astype(np.complex128)
     assert np.max(np.abs(got - ref)) <= 1e-5
+    assert abs(o["ground_prob"] - oracle.success_prob(ref, e)) <= 1e-6
     assert abs(o["ground_prob"] / o["norm"] - oracle.success_prob(ref, e)) <= 1e-6
 
 

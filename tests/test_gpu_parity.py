@@ -1,10 +1,11 @@
 """GPU parity: the CUDA path (through the C ABI) against the complex128 oracle.
 
 Bars (stated for the method): E(x) bit exact; max amplitude error <= 1e-5 for the
-FP32 path; probabilities within 1e-6.  Probabilities are compared as Born
-probabilities of the normalised state, P / ||psi||^2 (both sums in FP64): the
-FP32 state's norm drifts by a random walk of table and butterfly roundings
-(measured below 2e-6 over 400 steps), which is checked separately (NORM_TOL).  Sizes span the on-chip evolver (n <= 14),
+FP32 path; probabilities within 1e-6.  The ground-state probability is checked
+as returned (raw) and as the Born probability of the normalised state,
+P / ||psi||^2, both within 1e-6.  Every low pass folds the FP32 state's norm
+back to its starting value (the norm fold), so the norm itself stays within
+1e-6 (NORM_TOL) instead of drifting by a random walk of roundings.  Sizes span the on-chip evolver (n <= 14),
 the two-group streaming plan (n = 15..20, every strided width 5..10) and the
 three-group plan (n >= 21), with ragged widths.
 """
@@ -19,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 AMP_TOL = 1e-5
 PROB_TOL = 1e-6
-NORM_TOL = 5e-6
+NORM_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -159,6 +160,7 @@ def test_evolve_matches_oracle_strang(q, torch, n, src, T, K):
     err = np.max(np.abs(got - ref))
     assert err <= AMP_TOL, err
     p_ref = oracle.success_prob(ref, e)
+    assert abs(obs["ground_prob"] - p_ref) <= PROB_TOL, (obs, p_ref)
     assert abs(obs["ground_prob"] / obs["norm"] - p_ref) <= PROB_TOL, (obs, p_ref)
     assert abs(obs["norm"] - 1.0) <= NORM_TOL
     assert obs["ground_count"] == int(np.count_nonzero(e == 0))
@@ -269,9 +271,12 @@ def test_observables_match_oracle(q, torch, n):
 TC_CASES = [(15, 3.0, 20), (17, 3.0, 12), (20, 10.0, 200), (21, 1.0, 4)]
 
 
-@pytest.mark.parametrize("kind,amp_tol,prob_tol", [(1, AMP_TOL, PROB_TOL), (2, 1e-3, 1e-4)], ids=["bf16x3", "bf16x2"])
+# The BF16x2 ablation's per-step rounding is ~2^-16, so the norm left by its
+# last step (after the fold of the step before) is held to 1e-5.
+@pytest.mark.parametrize("kind,amp_tol,prob_tol,norm_tol", [(1, AMP_TOL, PROB_TOL, NORM_TOL), (2, 1e-3, 1e-4, 1e-5)],
+                         ids=["bf16x3", "bf16x2"])
 @pytest.mark.parametrize("n,T,K", TC_CASES, ids=[f"n{c[0]}-K{c[2]}" for c in TC_CASES])
-def test_tensor_core_variant_matches_oracle(q, torch, kind, amp_tol, prob_tol, n, T, K):
+def test_tensor_core_variant_matches_oracle(q, torch, kind, amp_tol, prob_tol, norm_tol, n, T, K):
     cl = satgen.load_instance("planted_n20_s0")["clauses"] if n == 20 else satgen.planted_instance(n, 11)["clauses"]
     e = oracle.violated_counts(n, cl)
     ref = oracle.evolve_strang(n, cl, T, K, energies=e)
@@ -283,7 +288,9 @@ def test_tensor_core_variant_matches_oracle(q, torch, kind, amp_tol, prob_tol, n
     inst.evolve(psi, T, K)
     o = inst.observables(psi)
     assert np.max(np.abs(to_np(psi) - ref)) <= amp_tol
+    assert abs(o["ground_prob"] - oracle.success_prob(ref, e)) <= prob_tol
     assert abs(o["ground_prob"] / o["norm"] - oracle.success_prob(ref, e)) <= prob_tol
+    assert abs(o["norm"] - 1.0) <= norm_tol
 
 
 # ------------------------------------------------ rotation form (variant 3) ---
@@ -308,6 +315,7 @@ def test_rotation_form_matches_oracle(q, torch, n, T, K):
     inst.evolve(psi, T, K)
     o = inst.observables(psi)
     assert np.max(np.abs(to_np(psi) - ref)) <= AMP_TOL
+    assert abs(o["ground_prob"] - oracle.success_prob(ref, e)) <= PROB_TOL
     assert abs(o["ground_prob"] / o["norm"] - oracle.success_prob(ref, e)) <= PROB_TOL
     assert abs(o["norm"] - 1.0) <= NORM_TOL
     inst.close()

@@ -90,8 +90,9 @@ def test_persistent_requests_match_oracle(env, n, T, K, monkeypatch):
     with q.Server(max_slots=4) as srv:
         r = next(iter(wait_all(srv, [srv.submit(n, cl, T, K)]).values()))
     assert r["status"] == 0
+    assert abs(r["success_prob"] - oracle.success_prob(ref, e)) <= 1e-6
     assert abs(r["success_prob"] / r["norm"] - oracle.success_prob(ref, e)) <= 1e-6
-    assert abs(r["norm"] - 1.0) <= 5e-6
+    assert abs(r["norm"] - 1.0) <= 1e-6
     assert abs(r["energy"] - oracle.expect_hp(ref, e)) <= 1e-4
     assert abs(r["expect_hb"] - oracle.expect_hb(n, ref)) <= 1e-4
 
@@ -105,6 +106,7 @@ def test_batched_result_matches_oracle(env):
     with q.Server(max_slots=8) as srv:
         r = wait_all(srv, [srv.submit(n, cl, T, K)])
     r = next(iter(r.values()))
+    assert abs(r["success_prob"] - oracle.success_prob(ref, e)) <= 1e-6
     assert abs(r["success_prob"] / r["norm"] - oracle.success_prob(ref, e)) <= 1e-6
     assert abs(r["energy"] - oracle.expect_hp(ref, e)) <= 1e-5
     assert abs(r["expect_hb"] - oracle.expect_hb(n, ref)) <= 1e-5
@@ -192,3 +194,39 @@ def test_stuck_grid_barrier_times_out_and_the_server_recovers(env):
         assert r["status"] == 0
         ref = alone(q, torch, n, inst[n], T, K)
         assert abs(r["success_prob"] - ref["ground_prob"]) <= 1e-6
+
+
+def overlapping_pairs(rs):
+    out = []
+    for i in range(len(rs)):
+        for j in range(i + 1, len(rs)):
+            a, b = rs[i], rs[j]
+            if max(a["t_dev_start"], b["t_dev_start"]) < min(a["t_dev_end"], b["t_dev_end"]):
+                out.append((i, j))
+    return out
+
+
+def test_requests_overlap_on_the_device(env):
+    """Requests admitted together are in flight on the GPU at the same time:
+    their device intervals (events on the request's own stream, before its
+    first copy and after its results' read-back, on the device clock) overlap
+    -- mid-size requests run as persistent launches on disjoint SMs, larger
+    ones interleave their passes on the issuer streams -- and each result is
+    still the same, bit for bit, as the same request served alone."""
+    q, _ = env
+    reqs = [(16, 60 + i, 10.0, 200) for i in range(4)] + [(20, 70 + i, 5.0, 100) for i in range(4)]
+    insts = {seed: satgen.planted_instance(n, seed)["clauses"] for n, seed, _, _ in reqs}
+    with q.Server(max_slots=16) as srv:
+        tickets = [srv.submit(n, insts[seed], T, K) for n, seed, T, K in reqs]
+        res = wait_all(srv, tickets)
+    rs = [res[t] for t in tickets]
+    for r in rs:
+        assert r["status"] == 0
+        assert 0.0 <= r["t_dev_start"] < r["t_dev_end"]
+    assert overlapping_pairs(rs[:4]), [(r["t_dev_start"], r["t_dev_end"]) for r in rs[:4]]
+    assert overlapping_pairs(rs[4:]), [(r["t_dev_start"], r["t_dev_end"]) for r in rs[4:]]
+    keys = ("success_prob", "norm", "energy", "expect_hb", "ground_count")
+    with q.Server(max_slots=4) as one:
+        for (n, seed, T, K), r in zip(reqs, rs):
+            solo = next(iter(wait_all(one, [one.submit(n, insts[seed], T, K)]).values()))
+            assert all(r[k] == solo[k] for k in keys), (n, r, solo)

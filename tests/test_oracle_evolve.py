@@ -257,3 +257,27 @@ def test_midpoint_schedule_is_second_order_in_time():
     # the Strang split with the same schedule is second order to the same solution
     st = [np.max(np.abs(oracle.evolve_strang(n, cl, T, K) - ref)) for K in (20, 40, 80)]
     assert all(3.5 < st[i] / st[i + 1] < 4.5 for i in range(2)), st
+
+
+def test_block_instance_factorises():
+    """A block instance (clauses never mix blocks) evolves as the tensor product
+    of its blocks' Strang states, with the ground-state probability the product
+    of theirs: the full-size GPU checks at 30 and 32 qubits rest on this."""
+    d = satgen.block_instance(12, 3, 12, 6, seed=9)
+    T, K = 2.0, 16
+    full = oracle.evolve_strang(12, d["clauses"], T, K)
+    x = np.arange(1 << 12)
+    prod = np.ones(1 << 12, dtype=complex)
+    p_blocks = 1.0
+    for blk in d["blocks"]:
+        nb = len(blk["vars"])
+        e = oracle.violated_counts(nb, blk["clauses"])
+        psi = oracle.evolve_strang(nb, blk["clauses"], T, K, energies=e)
+        loc = np.zeros(1 << 12, dtype=np.int64)
+        for k, v in enumerate(blk["vars"]):
+            loc |= ((x >> (v - 1)) & 1) << k
+        prod *= psi[loc]
+        p_blocks *= oracle.success_prob(psi, e)
+    assert np.max(np.abs(full - prod)) <= 1e-12
+    e_full = oracle.violated_counts(12, d["clauses"])
+    assert abs(oracle.success_prob(full, e_full) - p_blocks) <= 1e-12

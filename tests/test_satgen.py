@@ -63,3 +63,30 @@ def test_ratio_instance_is_deterministic_and_degenerate_when_asked():
     assert a["solutions"] >= 2
     assert all(len(set(abs(l) for l in c)) == 3 for c in a["clauses"])
     assert satgen.count_solutions(14, a["clauses"]) == a["solutions"]
+
+
+def test_block_instance_structure_and_separable_energy():
+    import oracle
+    d = satgen.block_instance(12, 3, 20, 10, seed=4)
+    assert d["m"] == 3 * 30 == len(d["clauses"])
+    owner = {}
+    for b, blk in enumerate(d["blocks"]):
+        assert blk["vars"] == [v for v in range(1, 13) if (v - 1) % 3 == b]
+        for v in blk["vars"]:
+            owner[v] = b
+    for lits in d["clauses"]:
+        assert len({owner[abs(l)] for l in lits}) == 1  # no clause mixes blocks
+        assert len({abs(l) for l in lits}) == 3
+    # E(x) is the sum of the blocks' energies on their own variables
+    e = oracle.violated_counts(12, d["clauses"])
+    x = np.arange(1 << 12)
+    total = np.zeros(1 << 12, dtype=np.int64)
+    for blk in d["blocks"]:
+        loc = np.zeros(1 << 12, dtype=np.int64)
+        for k, v in enumerate(blk["vars"]):
+            loc |= ((x >> (v - 1)) & 1) << k
+        total += oracle.violated_counts(len(blk["vars"]), blk["clauses"])[loc]
+    assert np.array_equal(e, total)
+    # the planted assignment satisfies everything; its complement violates every repeated clause
+    assert e[d["planted"]] == 0
+    assert e[(1 << 12) - 1 - d["planted"]] >= 3 * 10
