@@ -5,9 +5,11 @@ Workload: the committed planted unique-solution instance with n = 30 variables
 (satgen/instances/planted_n30_s0.json, m = 371 clauses), complex64 state of
 2^30 amplitudes (8 GiB, far larger than L2, so no flush is needed between
 steps), linear schedule with dt = 0.1 (the T = 40, 400-step configuration).
-One "step" = one full second-order Strang step: P phase (violated clauses
-computed on the fly), forward Walsh-Hadamard transform, popcount phase, inverse
-transform, i.e. the 2g-2 = 4 fused HBM passes of the three-group plan.
+One "step" = one full second-order Strang step of Eq. (1) frozen at the step's
+midpoint: the merged half phases of H_P (violated-clause counts), and
+exp(-i dt (1-s) H_B) applied as Walsh-Hadamard sandwiches on every 5-qubit
+block (the default rotation form), i.e. g = 3 HBM round trips at n = 30: the
+two strided groups' passes and the low pass.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -42,10 +44,9 @@ FALLBACK_HBM_GBS = 6800.0
 # the capture; a mismatch (kernel changed since) reports traffic = null.
 TRAFFIC = {
     # ncu full-set capture of sp_tma_kernel<10,4,2> (the default rotation form's
-    # strided pass, 128-byte runs) on the n=28 instance with QAA_GROUP_BITS=10,8
-    # (profiles/sp_tma_kernel_q10_run128_rotation_n28.md): 2.147558e9 + 2.087137e9
-    # bytes per launch for 2^28 amplitudes, scaled by the amplitude count (x4) to
-    # one n=30 launch.
+    # strided pass, 128-byte runs) on the 28-qubit instance with
+    # QAA_GROUP_BITS=10,8: DRAM bytes read + written per launch for 2^28
+    # amplitudes, scaled by the amplitude count (x4) to one 30-qubit launch.
     "strided": {"bytes_per_launch": 4 * (2.147558e9 + 2.087137e9), "src_sha": "56a58091bcd0fb80"},
 }
 

@@ -12,9 +12,13 @@
  * K second-order Strang steps of dt = T / K, step k frozen at s_k = (k + 1/2)/K:
  *   exp(-i dt/2 s_k H_P) W exp(-i dt (1 - s_k) popcount) W exp(-i dt/2 s_k H_P),
  * W the normalised Walsh-Hadamard transform (H_B = W diag(popcount) W).  The
- * half phases of adjacent steps are merged, E(x) is recomputed from clause bit
- * masks inside the kernels (bit exact), and the popcount phase is applied between
- * two fused multi-qubit Walsh-Hadamard passes.
+ * half phases of adjacent steps are merged and E(x) comes from the clause bit
+ * masks, bit exact (counted inside the kernels, or stored once per instance as
+ * per-tile bit-sliced counts).  By default exp(-i theta H_B) is applied as a
+ * Walsh-Hadamard sandwich W diag(exp(-i theta popcount)) W on every 5-qubit
+ * block inside each pass (H_B is a sum of commuting one-qubit terms); the
+ * whole-register form (the popcount phase between two transforms of all n
+ * qubits) and tensor-core transforms are variants (qaa_set_variant).
  *
  * Index convention (Sec. 2.1, basis |q_n ... q_1>): amplitude psi[x] belongs to
  * the assignment with x_i = bit (i - 1) of x.
@@ -92,12 +96,18 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream);
 /*
  * qaa_set_variant -- choose the Walsh-Hadamard implementation of the
  * streaming passes (n >= 15; the on-chip path for n <= 14 is always FP32).
- *   wht_kind 0: FP32 CUDA-core butterflies (default).
- *            1: tensor cores, 16 x 16 Hadamard blocks on BF16 operands with the
- *               amplitude split into three BF16 parts (hi + mid + lo), FP32
- *               accumulation: about FP32 accuracy.
+ *   wht_kind 0: FP32 CUDA-core butterflies, the whole-register W.B.W form.
+ *            1: the W.B.W form with every transform on the tensor cores
+ *               (tcgen05): each group of <= 10 qubits in two 5-qubit stages,
+ *               each a GEMM against the exact +-1 block H_32 on BF16 operands,
+ *               the amplitude split into three BF16 parts (hi + mid + lo),
+ *               FP32 accumulation in tensor memory: about FP32 accuracy.  Its
+ *               low passes read the stored per-tile clause counts (see
+ *               qaa_evolve), which the handle then keeps whatever
+ *               QAA_LP_COUNTS says.
  *            2: as 1 with two parts (hi + lo): about 16 mantissa bits.
- *            3: rotation form: exp(-i theta H_B) applied directly as the product
+ *            3: rotation form (the default on the TMA passes): exp(-i theta H_B)
+ *               applied directly as the product
  *               of its n one-qubit factors (H_B = sum_i (1 - sigma^x_i)/2 is a
  *               sum of commuting one-qubit terms, Sec. 2.1), each
  *               (|+><+| + e^(-i theta) |-><-|), as complex butterflies inside
@@ -115,22 +125,6 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream);
  */
 int qaa_set_variant(qaa_handle h, int wht_kind, int q);
 
-/*
- * qaa_set_launch_mode -- how qaa_evolve* issue the streaming passes (n >= 15;
- * the on-chip path for n <= 14 is one launch per chunk either way).
- *   QAA_LAUNCH_PASSES (0, default): one kernel launch per pass from the host.
- *   QAA_LAUNCH_GRAPH  (1): one CUDA graph per step range, launched once: a
- *     WHILE conditional node whose body is 8 Strang steps, the phase rows of
- *     each iteration computed on the device from the same FP64 formulas, so
- *     the result is the same bit for bit.  The graph is kept and relaunched
- *     while psi, T, steps, the range, the schedule pointer, the variant and the
- *     stream stay the same; any change rebuilds it (a stream synchronisation
- *     and a few hundred microseconds of host time).  The handle allocates a
- *     small device scratch (the loop counter and 8 steps of phase rows) on the
- *     first graph launch.  The integrator is the paper's Eq. (1) Hamiltonian
- *     split as in qaa_evolve; the paper has no launch-graph counterpart.
- * Returns QAA_E_ARG for an unknown mode.
- */
 /*
  * qaa_autotune -- choose the pass plan of a streaming-size handle (n >= 15)
  * by timing candidates on the GPU.  Stage 1 times the default plan and every
@@ -190,6 +184,22 @@ int qaa_lowest_eigenvalues(qaa_handle h, double s, int k, int max_iter, int star
 /* Forget every plan recorded by qaa_autotune in this process. */
 int qaa_forget_tuned_plans(void);
 
+/*
+ * qaa_set_launch_mode -- how qaa_evolve* issue the streaming passes (n >= 15;
+ * the on-chip path for n <= 14 is one launch per chunk either way).
+ *   QAA_LAUNCH_PASSES (0, default): one kernel launch per pass from the host.
+ *   QAA_LAUNCH_GRAPH  (1): one CUDA graph per step range, launched once: a
+ *     WHILE conditional node whose body is 8 Strang steps, the phase rows of
+ *     each iteration computed on the device from the same FP64 formulas, so
+ *     the result is the same bit for bit.  The graph is kept and relaunched
+ *     while psi, T, steps, the range, the schedule pointer, the variant and the
+ *     stream stay the same; any change rebuilds it (a stream synchronisation
+ *     and a few hundred microseconds of host time).  The handle allocates a
+ *     small device scratch (the loop counter and 8 steps of phase rows) on the
+ *     first graph launch.  The integrator is the paper's Eq. (1) Hamiltonian
+ *     split as in qaa_evolve; the paper has no launch-graph counterpart.
+ * Returns QAA_E_ARG for an unknown mode.
+ */
 #define QAA_LAUNCH_PASSES 0
 #define QAA_LAUNCH_GRAPH 1
 int qaa_set_launch_mode(qaa_handle h, int mode);
@@ -206,6 +216,13 @@ int qaa_init_uniform(qaa_handle h, void* psi);
  * bytes per amplitude: 1.4 GiB at n = 30) so that later low passes read them
  * instead of counting again; if that memory cannot be allocated the passes
  * count on the fly (the same values).  QAA_LP_COUNTS=0 turns the store off.
+ * Norm fold: the exact evolution is unitary, and the low passes measure the
+ * FP32 state's norm (|psi|^2 summed in the pass, no extra read; every step for
+ * n >= 22, every 8 steps below) so that the next one scales its phase row
+ * back to the norm psi had at the start of the call (times the exact power of
+ * two of the unnormalised transforms): the norm stays within about 1e-7 of
+ * its starting value instead of drifting with the roundings (about 4e-6
+ * after 3200 steps at n = 20).
  */
 int qaa_evolve(qaa_handle h, void* psi, double T, int64_t steps);
 
@@ -317,6 +334,9 @@ int qaa_describe_plan(qaa_handle h, char* buf, size_t len);
  * QAA_E_ARG with a message in qaa_last_error().
  * The first call made on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is kept for the life of the process: after cudaDeviceReset on a
+ * device this entry point must not be used on it again (the reset unloads the
+ * module, and the kept address belongs to the old context).
  * All calls share the one array and it keeps the last call's contents: calls
  * whose work can overlap on the GPU (from several threads or streams) race and
  * must be serialised by the caller.

@@ -254,28 +254,28 @@ __device__ __forceinline__ float tile_norm(const float2 (&v)[32]) {
   return (fa.x + fb.x) + (fa.y + fb.y);
 }
 
-// Sum of one slot's partials, in the same fixed order in every CTA: lane i
-// takes partials i, i + 32, ..., then a shuffle tree; lane 0's value is
-// returned to every lane.  Called by one whole warp.
-__device__ __forceinline__ double fold_slot_sum(const double* __restrict__ slot, int lane) {
-  // L2 loads: within a persistent kernel the slot was written by other CTAs
-  // since this SM last read it
-  const int cnt = static_cast<int>(__ldcg(slot));
-  double s = 0.0;
-  for (int i = lane; i < cnt; i += 32) s += __ldcg(slot + 1 + i);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return __shfl_sync(0xffffffffu, s, 0);
-}
-
 // The correction factor of a low pass (1 when there is nothing to correct, or
 // when either sum is not a positive finite number), valid in lane 0.  One
-// whole warp calls it; only lane 0 does the scalar FP64 work (GB300's FP64
-// rate is a small fraction of its FP32 rate).
+// whole warp calls it: lane i adds partials i, i + 32, ... of both slots (the
+// loads of the two slots in flight together; L2 loads, since within a
+// persistent kernel the slots were written by other CTAs since this SM last
+// read them), then a shuffle tree in the same fixed order in every CTA; only
+// lane 0 does the scalar FP64 work (GB300's FP64 rate is a small fraction of
+// its FP32 rate).
 __device__ __forceinline__ double fold_factor(const NormFold& f, int lane) {
   if (!f.ref || !f.prev) return 1.0;
-  const double r = fold_slot_sum(f.ref, lane);
-  const double s = fold_slot_sum(f.prev, lane);
+  const int cr = static_cast<int>(__ldcg(f.ref)), cp = static_cast<int>(__ldcg(f.prev));
+  const int cnt = cr > cp ? cr : cp;
+  double r = 0.0, s = 0.0;
+  for (int i = lane; i < cnt; i += 32) {
+    if (i < cr) r += __ldcg(f.ref + 1 + i);
+    if (i < cp) s += __ldcg(f.prev + 1 + i);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r += __shfl_xor_sync(0xffffffffu, r, o);
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
   if (lane != 0) return 1.0;
   if (!(r > 0.0) || !(s > 0.0) || !isfinite(r) || !isfinite(s)) return 1.0;
   const double q = r / s;

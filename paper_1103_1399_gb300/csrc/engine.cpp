@@ -463,14 +463,26 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
                                "] for this variant");
   if (wht_kind == qaa::kRotationForm && h->n > qaa::kOnchipMaxBits && !h->plan.use_tma)
     return fail(QAA_E_ARG, "the rotation form needs the TMA passes (not available, or QAA_PASSES=classic)");
+  // the low pass the plan will use: 12 bits only for the rotation form on TMA
+  // passes with QAA_LOW_BITS=12 (and at least 5 bits above it)
+  int low = qaa::kLowBits;
+  if (wht_kind == qaa::kRotationForm && h->plan.use_tma) {
+    const char* lb = std::getenv("QAA_LOW_BITS");
+    if (lb && std::atoi(lb) == 12 && h->n - 12 >= 5) low = 12;
+  }
   if (q != 0 && h->n > qaa::kOnchipMaxBits) {
-    const int rest = h->n - qaa::kLowBits, ng = (rest + q - 1) / q;
-    if (5 * ng > rest)
-      return fail(QAA_E_ARG, "no split of the " + std::to_string(rest) + " strided bits into groups of 5.." +
+    auto splits = [&](int L) {
+      const int rest = h->n - L, ng = (rest + q - 1) / q;
+      return 5 * ng <= rest;
+    };
+    // a 12-bit low pass that leaves no split into groups of 5..q bits falls back to 10 bits
+    if (low == 12 && !splits(12)) low = qaa::kLowBits;
+    if (!splits(low))
+      return fail(QAA_E_ARG, "no split of the " + std::to_string(h->n - low) + " strided bits into groups of 5.." +
                                  std::to_string(q) + " bits");
   }
   if (q != 0)
-    qaa::make_default_plan(h->n, h->plan, q);  // groups of at most q bits (the fewest such groups)
+    qaa::make_default_plan(h->n, h->plan, q, low);  // groups of at most q bits (the fewest such groups)
   else
     qaa::make_plan(h->n, h->plan, widest);
   // a plan made (or tuned) for the other form gets the run lengths of this one

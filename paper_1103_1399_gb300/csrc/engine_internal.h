@@ -15,6 +15,12 @@ namespace qaa {
 // its literal false.  Returns 0, or a nonzero code with a message.
 int encode_clauses(int n, const int32_t* lits, int m, std::vector<ClauseMV>& mv, std::vector<ClauseLP>& lp,
                    std::string& err);
+// Clause c of lits (three signed literals) -> (mask, viol).
+int encode_clause(int n, const int32_t* lits, int c, ClauseMV& out, std::string& err);
+// The 1024-amplitude tile record of a clause (ClauseLP in qaa_internal.cuh).
+ClauseLP clause_lp(const ClauseMV& mv);
+// Every clause's tile record into a caller-provided array of m records.
+int encode_clauses_lp(int n, const int32_t* lits, int m, ClauseLP* out, std::string& err);
 
 constexpr int kRotationForm = 3;  // PassPlan::wht_kind of the rotation form
 

@@ -19,8 +19,8 @@
 #include <mutex>
 #include <string>
 
+#include "engine_internal.h"
 #include "qaa.h"
-#include "qaa_internal.cuh"
 
 namespace {
 
@@ -39,38 +39,6 @@ void* g_scratch_addr[kMaxDevices] = {};
 int noalloc_fail(int code, const std::string& msg) {
   qaa::set_last_error(msg);
   return code;
-}
-
-// Clause list -> per-tile clause records (the same encoding the handle builds).
-int encode_lp(int n, const int32_t* clauses, int m, qaa::ClauseLP* out) {
-  for (int c = 0; c < m; ++c) {
-    unsigned long long mask = 0, viol = 0;
-    int width = 0;
-    for (int k = 0; k < 3; ++k) {
-      const int32_t lit = clauses[3 * c + k];
-      if (lit == 0) continue;
-      const long long a = lit < 0 ? -static_cast<long long>(lit) : lit;
-      if (a > n) return noalloc_fail(QAA_E_ARG, "clause " + std::to_string(c) + ": literal beyond n");
-      const unsigned long long bit = 1ull << (a - 1);
-      if (mask & bit) return noalloc_fail(QAA_E_ARG, "clause " + std::to_string(c) + ": variable repeated");
-      mask |= bit;
-      if (lit < 0) viol |= bit;
-      ++width;
-    }
-    if (width == 0) return noalloc_fail(QAA_E_ARG, "clause " + std::to_string(c) + ": no literals");
-    unsigned p0 = 0, p5 = 0;
-    const unsigned m0 = static_cast<unsigned>(mask & 31u), v0 = static_cast<unsigned>(viol & 31u);
-    const unsigned m5 = static_cast<unsigned>((mask >> 5) & 31u), v5 = static_cast<unsigned>((viol >> 5) & 31u);
-    for (unsigned j = 0; j < 32; ++j) {
-      if ((j & m0) == v0) p0 |= 1u << j;
-      if ((j & m5) == v5) p5 |= 1u << j;
-    }
-    out[c].hi_mask = static_cast<unsigned>(mask >> qaa::kLowBits);
-    out[c].hi_viol = static_cast<unsigned>(viol >> qaa::kLowBits);
-    out[c].pat0 = p0;
-    out[c].pat5 = p5;
-  }
-  return QAA_OK;
 }
 
 }  // namespace
@@ -114,9 +82,13 @@ extern "C" int qaa_observables_noalloc(int n, const int32_t* clauses, int m, con
   double* d_partials = reinterpret_cast<double*>(base + kResultBytes);
   qaa::ClauseLP* d_clauses = reinterpret_cast<qaa::ClauseLP*>(base + kResultBytes + kPartialBytes);
 
+  // the handle's own encoding (plan.cpp), into a per-thread host table
   static thread_local qaa::ClauseLP host_table[QAA_MAX_CLAUSES];
-  int st = encode_lp(n, clauses, m, host_table);
-  if (st) return st;
+  {
+    std::string msg;
+    const int st = qaa::encode_clauses_lp(n, clauses, m, host_table, msg);
+    if (st) return noalloc_fail(st, msg);
+  }
 
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   if (m > 0) {

@@ -25,11 +25,11 @@
 // block): bit-identical run to run.
 //
 // Passes over the state: the low kernel reads it once (bits 0..9 of the index
-// in one warp's 1024-amplitude tile: the norm-type sums and the pair
-// correlations of bits 0..9), and bits 10..n-1 are covered in groups of at
-// most 10 bits by read-only strided-tile passes (corr_tma_kernel in
-// tma_kernels.cu; plain loads in groups of 5 when TMA is unavailable): 3 reads
-// of the state at n = 30.
+// in one warp's 1024-amplitude tile, brought in by a bulk copy for n > 10: the
+// norm-type sums and the pair correlations of bits 0..9), and bits 10..n-1 are
+// covered in groups of at most 10 bits by read-only strided-tile passes
+// (corr_tma_kernel in tma_kernels.cu; plain loads in groups of 5 when TMA is
+// unavailable): 3 reads of the state at n = 30.
 #include "device_common.cuh"
 
 namespace qaa {
@@ -247,6 +247,138 @@ __global__ void __launch_bounds__(kObsWarps * 32)
   }
 }
 
+// ---- bulk-copy pipelined low kernel (n > 10) ---------------------------------
+__device__ __forceinline__ uint32_t obs_smem(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool obs_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(obs_smem(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool obs_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < (1ll << 24); ++it)
+    if (obs_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void obs_bulk_load(void* dst, const void* src, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(obs_smem(bar)), "r"(8192u) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 8192, [%2];" ::"r"(
+                   obs_smem(dst)),
+               "l"(src), "r"(obs_smem(bar))
+               : "memory");
+}
+
+struct ObsTmaLayout {
+  size_t off_warp, per_warp, off_bar, off_red, total;
+  __host__ __device__ ObsTmaLayout(int m, bool stored) {
+    off_warp = stored ? 0 : ((16u * static_cast<size_t>(m) + 127u) & ~static_cast<size_t>(127));
+    per_warp = 8u * kObsRow * 32u + (stored ? 0u : 8u * static_cast<size_t>(m + 16));
+    per_warp = (per_warp + 127u) & ~static_cast<size_t>(127);
+    off_bar = off_warp + per_warp * kObsWarps;
+    off_red = off_bar + 8u * kObsWarps;
+    total = off_red + 64u * 8u;
+  }
+};
+
+// As obs_low_kernel for n > 10, with each warp's 1024-amplitude tile brought in
+// by a 1-D cp.async.bulk into its shared buffer (mbarrier completion): the
+// buffer is read into registers and reused for the transpose, and the next
+// tile's copy is issued as soon as the transpose is read back, so that it is
+// in flight during this tile's double-float sums.  The (norm, <H_P>) pairs
+// are added into FP64 every other tile.
+template <bool STORED>
+__global__ void __launch_bounds__(kObsWarps * 32, 2)
+    obs_tma_kernel(const float2* __restrict__ psi, int n, int m, const ClauseLP* __restrict__ cl,
+                   const unsigned* __restrict__ counts, long long ntiles, double* __restrict__ partials,
+                   int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const ObsTmaLayout L(m, STORED);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
+  unsigned char* wbase = smem + L.off_warp + L.per_warp * warp;
+  float2* s_buf = reinterpret_cast<float2*>(wbase);
+  uint2* s_act = reinterpret_cast<uint2*>(wbase + 8u * kObsRow * 32u);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp;
+  double* s_red = reinterpret_cast<double*>(smem + L.off_red);
+  const long long step = static_cast<long long>(gridDim.x) * kObsWarps;
+  const long long first = static_cast<long long>(blockIdx.x) * kObsWarps + warp;
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(obs_smem(s_bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (lane == 0 && first < ntiles) obs_bulk_load(s_buf, psi + (first << kLowBits), s_bar);
+  if (!STORED) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
+  }
+  __syncthreads();
+  double d_norm = 0.0, d_hp = 0.0, d_gp = 0.0, d_gc = 0.0, d_corr = 0.0;
+  ObsAcc a;
+  int it = 0;
+  bool ok = true;
+  for (long long tile = first; tile < ntiles; tile += step, ++it) {
+    ok = obs_wait(s_bar, static_cast<uint32_t>(it) & 1u);
+    if (__any_sync(0xffffffffu, !ok)) break;
+    float2 v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = s_buf[lane + 32 * r];
+    unsigned long long c2 = reg_pairs(v, 5, n, 0ull);  // index bits 5..9
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) s_buf[lane + kObsRow * r] = v[r];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = s_buf[kObsRow * lane + r];
+    __syncwarp();
+    const long long tn = tile + step;
+    if (lane == 0 && tn < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      obs_bulk_load(s_buf, psi + (tn << kLowBits), s_bar);
+    }
+    c2 = reg_pairs(v, 0, n, c2);  // index bits 0..4
+    unsigned pl[kPlanes];
+    int nconst;
+    if (STORED) {
+      load_counts(counts, tile, lane, pl, nconst);
+    } else {
+      int npad;
+      fold_tile<true>(s_cl, m, static_cast<unsigned>(tile), lane, s_act, nconst, npad);
+      count_active(s_act, npad, 1u << lane, pl);
+    }
+    ObsAddUnroll<0>::run(a, v, pl, nconst, lane, 1 << kLowBits);
+    const float2 c = bits_f2(c2);
+    d_corr += static_cast<double>(c.x + c.y);
+    if ((it & 1) || tn >= ntiles) {
+      const float2 ss = bits_f2(a.s), ee = bits_f2(a.e);
+      d_norm += static_cast<double>(ss.x) + static_cast<double>(ee.x);
+      d_hp += static_cast<double>(ss.y) + static_cast<double>(ee.y);
+      if (a.gc != 0.f) {
+        d_gp += static_cast<double>(a.gs) + static_cast<double>(a.ge);
+        d_gc += static_cast<double>(a.gc);
+      }
+      a = ObsAcc();
+    }
+  }
+  if (!ok) {
+    if (lane == 0) atomicExch(err, 1);
+  } else if (lane == 0) {
+    // a copy may be in flight if the loop was left early; wait for it (bounded)
+    const long long t = first + static_cast<long long>(it) * step;
+    if (t < ntiles && !obs_wait(s_bar, static_cast<uint32_t>(it) & 1u)) atomicExch(err, 1);
+  }
+  const double q[kObsQuant] = {d_norm, d_hp, d_gp, d_gc, d_corr};
+#pragma unroll
+  for (int k = 0; k < kObsQuant; ++k) {
+    const double t = block_sum(q[k], s_red);
+    if (threadIdx.x == 0) partials[static_cast<size_t>(k) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 // Pair correlations for index bits [a, a+w) (a >= 10, w <= 5) with plain
 // loads: one thread per column (the other index bits), coalesced over the low
 // bits.  Used for n = 11..14 and when TMA is unavailable.
@@ -311,7 +443,7 @@ static int obs_grid(int num_sms) { return 2 * num_sms; }
 // plain loads (and always for n - 10 < 5).
 struct CorrPlan {
   int ng = 0;
-  int a[8] = {}, q[8] = {};
+  int a[8] = {}, a2[8] = {}, q[8] = {};
   bool tma = false;
 };
 static CorrPlan corr_plan(int n, bool allow_tma) {
@@ -325,7 +457,17 @@ static CorrPlan corr_plan(int n, bool allow_tma) {
   for (int g = 0; g < p.ng; ++g) {
     p.q[g] = rest / p.ng + (g < rest % p.ng ? 1 : 0);
     p.a[g] = a;
+    p.a2[g] = a + 5;
     a += p.q[g];
+  }
+  // two 10-bit groups (n = 30): {10..14, 25..29} and {15..24}, as the
+  // evolution's plan, so that a tile's rows span at most 128 memory pages
+  // (the contiguous group [20, 30) ran at a third of the read bandwidth)
+  if (p.tma && p.ng == 2 && p.q[0] == 10 && p.q[1] == 10) {
+    p.a[0] = kLowBits;
+    p.a2[0] = kLowBits + 15;
+    p.a[1] = kLowBits + 5;
+    p.a2[1] = kLowBits + 10;
   }
   return p;
 }
@@ -351,17 +493,27 @@ cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, in
   const int P = obs_grid(lc.num_sms);
   const long long ntiles = n > kLowBits ? (1ll << (n - kLowBits)) : 1ll;
   const bool stored = counts != nullptr && n > kLowBits;
-  auto kern = stored ? obs_low_kernel<true> : obs_low_kernel<false>;
-  cudaError_t err = allow_smem(reinterpret_cast<const void*>(kern), obs_low_smem(QAA_MAX_CLAUSES_DEV, stored));
-  if (err != cudaSuccess) return err;
-  kern<<<P, kObsWarps * 32, obs_low_smem(m, stored), lc.stream>>>(psi, n, m, cl, counts, ntiles, partials);
+  cudaError_t err;
+  if (n > kLowBits && err_word != nullptr && reinterpret_cast<uintptr_t>(psi) % 16u == 0) {
+    // whole tiles: the bulk-copy pipelined kernel
+    auto kern = stored ? obs_tma_kernel<true> : obs_tma_kernel<false>;
+    err = allow_smem(reinterpret_cast<const void*>(kern), ObsTmaLayout(QAA_MAX_CLAUSES_DEV, stored).total);
+    if (err != cudaSuccess) return err;
+    kern<<<P, kObsWarps * 32, ObsTmaLayout(m, stored).total, lc.stream>>>(psi, n, m, cl, counts, ntiles, partials,
+                                                                          err_word);
+  } else {
+    auto kern = stored ? obs_low_kernel<true> : obs_low_kernel<false>;
+    err = allow_smem(reinterpret_cast<const void*>(kern), obs_low_smem(QAA_MAX_CLAUSES_DEV, stored));
+    if (err != cudaSuccess) return err;
+    kern<<<P, kObsWarps * 32, obs_low_smem(m, stored), lc.stream>>>(psi, n, m, cl, counts, ntiles, partials);
+  }
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   // the TMA passes need an error word for their bounded waits
   const CorrPlan cp = corr_plan(n, err_word != nullptr && reinterpret_cast<uintptr_t>(psi) % 16u == 0);
   for (int k = 0; k < cp.ng; ++k) {
     double* part = partials + static_cast<size_t>(kObsQuant + k) * P;
     if (cp.tma) {
-      err = launch_corr_tma(lc, psi, n, cp.a[k], cp.q[k], part, P, err_word);
+      err = launch_corr_tma(lc, psi, n, cp.a[k], cp.a2[k], cp.q[k], part, P, err_word);
     } else {
       const long long ncols = 1ll << (n - cp.q[k]);
       corr_kernel<<<P, 256, 0, lc.stream>>>(psi, cp.a[k], cp.q[k], ncols, part);

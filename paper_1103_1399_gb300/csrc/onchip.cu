@@ -191,7 +191,9 @@ __device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseM
     const float2* brow = btab + static_cast<size_t>(j) * (n + 1);
     const bool last = j == nsteps - 1;
     const unsigned pre = (j == 0 && first_p) ? kPreP : 0u;
-    const unsigned nrm = last ? 0u : kNorm;
+    // measure every fold_period(n)-th step; the factor corrects the step after it only
+    const bool measure = !last && (j + 1) % fold_period(n) == 0;
+    const unsigned nrm = measure ? kNorm : 0u;
     float nacc = 0.0f;
     if (G == 1) {
       const unsigned f = pre | (w0_done ? 0u : kW1) | kMidB | kW2 | kPostP | (last ? 0u : kW3) | nrm;
@@ -203,7 +205,7 @@ __device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseM
       for (int g = G - 2; g >= 1; --g) round_dispatch(s_psi, s_e, n, g, kW1, p_first, brow, p_next, cs, &nacc);
       round_dispatch(s_psi, s_e, n, 0, kW1 | kPostP | (last ? 0u : kW3) | nrm, p_first, brow, p_next, cs, &nacc);
     }
-    if (!last) cs = static_cast<float>(onchip_fold(nacc, nref > 0.0 ? nref : -1.0));
+    cs = measure ? static_cast<float>(onchip_fold(nacc, nref > 0.0 ? nref : -1.0)) : 1.0f;
     w0_done = !last;
   }
   for (int x = threadIdx.x; x < N; x += blockDim.x) psi[x] = s_psi[oswz(x)];

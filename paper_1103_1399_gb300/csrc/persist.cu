@@ -93,7 +93,7 @@ __device__ void low_pass(const PersistArgs& A, const ClauseLP* s_cl, float2* s_t
   const long long ntiles = 1ll << (A.n - kLowBits);
   Pass fp{};
   fp.rel = rel;
-  const NormFold nf = fold_for(A.fold, fp);
+  const NormFold nf = fold_for(A.fold, fp, fold_period(A.n));
   const float fc = static_cast<float>(fold_factor_block(nf));
   double nacc = 0.0;
   for (long long tile = static_cast<long long>(blockIdx.x) * kPersistWarps + warp; tile < ntiles;

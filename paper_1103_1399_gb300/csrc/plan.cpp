@@ -22,48 +22,68 @@
 
 namespace qaa {
 
+int encode_clause(int n, const int32_t* lits, int c, ClauseMV& out, std::string& err) {
+  unsigned long long mask = 0, viol = 0;
+  int width = 0;
+  for (int k = 0; k < 3; ++k) {
+    const int32_t lit = lits[3 * c + k];
+    if (lit == 0) continue;
+    const long long a = lit < 0 ? -static_cast<long long>(lit) : lit;
+    if (a > n) {
+      err = "clause " + std::to_string(c) + ": literal beyond n";
+      return QAA_E_ARG;
+    }
+    const unsigned long long bit = 1ull << (a - 1);
+    if (mask & bit) {
+      err = "clause " + std::to_string(c) + ": variable repeated in a clause";
+      return QAA_E_ARG;
+    }
+    mask |= bit;
+    if (lit < 0) viol |= bit;
+    ++width;
+  }
+  if (width == 0) {
+    err = "clause " + std::to_string(c) + ": no literals";
+    return QAA_E_ARG;
+  }
+  out = {mask, viol};
+  return QAA_OK;
+}
+
+ClauseLP clause_lp(const ClauseMV& mv) {
+  ClauseLP e;
+  e.hi_mask = static_cast<unsigned>(mv.mask >> kLowBits);
+  e.hi_viol = static_cast<unsigned>(mv.viol >> kLowBits);
+  unsigned p0 = 0, p5 = 0;
+  const unsigned m0 = static_cast<unsigned>(mv.mask & 31u), v0 = static_cast<unsigned>(mv.viol & 31u);
+  const unsigned m5 = static_cast<unsigned>((mv.mask >> 5) & 31u), v5 = static_cast<unsigned>((mv.viol >> 5) & 31u);
+  for (unsigned j = 0; j < 32; ++j) {
+    if ((j & m0) == v0) p0 |= 1u << j;
+    if ((j & m5) == v5) p5 |= 1u << j;
+  }
+  e.pat0 = p0;
+  e.pat5 = p5;
+  return e;
+}
+
+int encode_clauses_lp(int n, const int32_t* lits, int m, ClauseLP* out, std::string& err) {
+  for (int c = 0; c < m; ++c) {
+    ClauseMV mv;
+    const int st = encode_clause(n, lits, c, mv, err);
+    if (st) return st;
+    out[c] = clause_lp(mv);
+  }
+  return QAA_OK;
+}
+
 int encode_clauses(int n, const int32_t* lits, int m, std::vector<ClauseMV>& mv, std::vector<ClauseLP>& lp,
                    std::string& err) {
   mv.resize(static_cast<size_t>(m));
   lp.resize(static_cast<size_t>(m));
   for (int c = 0; c < m; ++c) {
-    unsigned long long mask = 0, viol = 0;
-    int width = 0;
-    for (int k = 0; k < 3; ++k) {
-      const int32_t lit = lits[3 * c + k];
-      if (lit == 0) continue;
-      const long long a = lit < 0 ? -static_cast<long long>(lit) : lit;
-      if (a > n) {
-        err = "clause " + std::to_string(c) + ": literal beyond n";
-        return QAA_E_ARG;
-      }
-      const unsigned long long bit = 1ull << (a - 1);
-      if (mask & bit) {
-        err = "clause " + std::to_string(c) + ": variable repeated in a clause";
-        return QAA_E_ARG;
-      }
-      mask |= bit;
-      if (lit < 0) viol |= bit;
-      ++width;
-    }
-    if (width == 0) {
-      err = "clause " + std::to_string(c) + ": no literals";
-      return QAA_E_ARG;
-    }
-    mv[c] = {mask, viol};
-    ClauseLP e;
-    e.hi_mask = static_cast<unsigned>(mask >> kLowBits);
-    e.hi_viol = static_cast<unsigned>(viol >> kLowBits);
-    unsigned p0 = 0, p5 = 0;
-    const unsigned m0 = static_cast<unsigned>(mask & 31u), v0 = static_cast<unsigned>(viol & 31u);
-    const unsigned m5 = static_cast<unsigned>((mask >> 5) & 31u), v5 = static_cast<unsigned>((viol >> 5) & 31u);
-    for (unsigned j = 0; j < 32; ++j) {
-      if ((j & m0) == v0) p0 |= 1u << j;
-      if ((j & m5) == v5) p5 |= 1u << j;
-    }
-    e.pat0 = p0;
-    e.pat5 = p5;
-    lp[c] = e;
+    const int st = encode_clause(n, lits, c, mv[c], err);
+    if (st) return st;
+    lp[c] = clause_lp(mv[c]);
   }
   return QAA_OK;
 }
@@ -377,7 +397,7 @@ cudaError_t allow_smem(const void* func, size_t bytes) {
 cudaError_t launch_planned_pass(const LaunchCtx& lc, const PassPlan& plan, const Pass& p, float2* psi, int m,
                                 const ClauseLP* cl, const float2* ptab, const float2* btab, int* err, const unsigned* counts,
                                 double* fold) {
-  const NormFold nf = fold_for(fold, p);
+  const NormFold nf = fold_for(fold, p, fold_period(plan.n));
   if (plan.wht_kind == kRotationForm) return launch_pass_tma(lc, p, psi, plan.n, m, cl, ptab, btab, err, counts, nf);
   if (plan.wht_kind)
     return launch_pass_tc(lc, p, psi, plan.n, m, cl, ptab, btab, plan.wht_kind == 1 ? 3 : 2, err, counts, nf);

@@ -75,39 +75,58 @@ struct Pass {
 // The exact evolution is unitary, but the FP32 state's norm performs a random
 // walk of roundings (about 4e-6 after 3200 Strang steps at 20 qubits, most of it
 // from the rounding of the few large amplitudes, so that the ground-state
-// probability drifts with it).  Every low pass therefore also sums |psi|^2 of
-// its output (FP32 per 1024-amplitude tile, FP64 beyond, one partial per CTA),
-// and the next step's low pass multiplies its P row by
+// probability drifts with it).  A low pass therefore also sums |psi|^2 of its
+// output (FP32 per 1024-amplitude tile, FP64 beyond, one partial per CTA), and
+// the next one multiplies its P row by
 //   c = sqrt(N_ref 2^j / N),
-// N the previous step's sum, N_ref the sum taken by the first pass of the range
-// and 2^j the power of two nearest to N / N_ref (the unnormalised
-// Walsh-Hadamard stages and the 2^-n factor scale the norm by exact powers of
-// two between passes).  Each correction restores the norm the range started
-// with up to that step's rounding, so the corrections do not accumulate.
+// N that sum, N_ref the sum taken by the first pass of the range and 2^j the
+// power of two nearest to N / N_ref (the unnormalised Walsh-Hadamard stages and
+// the 2^-n factor scale the norm by exact powers of two between passes).  Each
+// correction restores the norm the range started with up to the rounding of
+// the steps since the last one, so the corrections do not accumulate.  When
+// the state has concentrated on a few amplitudes the norm's error is mostly
+// theirs, so the correction also takes out most of their magnitude error.
+// Period F (fold_period): every step for n >= kFoldEveryStepBits, where the
+// extra reads are far below 1 % of a pass; every 8 steps below, where a pass
+// lasts microseconds (8: launch-graph bodies of 8 steps stay uniform).
 // Slots of kFoldSlot doubles: [0] = number of partials, then one per CTA.
-// Slot 0 holds the range's reference, slots 1 and 2 alternate by step.
+// Slot 0 holds the range's reference; F = 1 alternates slots 1 and 2 by step
+// parity (a pass reads one and writes the other), F = 8 uses slot 1.
 constexpr int kFoldSlot = 2048;
+constexpr int kFoldEveryStepBits = 22;
 constexpr size_t kFoldBytes = 3 * kFoldSlot * sizeof(double);
+__host__ __device__ inline int fold_period(int n) { return n >= kFoldEveryStepBits ? 1 : 8; }
 struct NormFold {
   double* out = nullptr;         // slot this launch writes (null: none)
   double* out2 = nullptr;        // a second slot written with the same partials
   const double* ref = nullptr;   // the range's reference slot (null: no correction)
-  const double* prev = nullptr;  // the previous step's slot
+  const double* prev = nullptr;  // the slot of the step to correct for
 };
-// Slots of a low pass with relative step p.rel: the first pass writes the
-// reference and the slot its first merged step reads; step r reads the slot of
-// step r - 1 and writes its own.
-__host__ __device__ inline NormFold fold_for(double* base, const Pass& p) {
+// Slots of a low pass with relative step p.rel and period F: the first pass
+// writes the reference and the slot step 0 reads (so that step 0's correction
+// is exactly 1); step r reads when r is a multiple of F and measures when
+// r + 1 is.
+__host__ __device__ inline NormFold fold_for(double* base, const Pass& p, int F) {
   NormFold f;
   if (!base || p.rel < -1) return f;
+  double* s1 = base + kFoldSlot;
+  double* s2 = base + 2 * kFoldSlot;
   if (p.rel == -1) {
     f.out = base;
-    f.out2 = base + 2 * kFoldSlot;
+    f.out2 = F == 1 ? s2 : s1;
     return f;
   }
-  f.out = base + (1 + (p.rel & 1)) * kFoldSlot;
-  f.ref = base;
-  f.prev = base + (1 + ((p.rel + 1) & 1)) * kFoldSlot;
+  if (F == 1) {
+    f.ref = base;
+    f.prev = (p.rel & 1) ? s1 : s2;
+    f.out = (p.rel & 1) ? s2 : s1;
+    return f;
+  }
+  if (p.rel % F == 0) {
+    f.ref = base;
+    f.prev = s1;
+  }
+  if ((p.rel + 1) % F == 0) f.out = s1;
   return f;
 }
 
@@ -165,10 +184,11 @@ size_t obs_partials_len(int n, int num_sms);
 cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, int m,
                                const ClauseLP* cl, double* partials, double* result,
                                const unsigned* counts = nullptr, int* err = nullptr);
-// Read-only TMA pass: pair correlations of index bits [a, a+q) (5 <= q <= 10),
-// one partial per CTA in partials[0 .. nparts).
-cudaError_t launch_corr_tma(const LaunchCtx& lc, const float2* psi, int n, int a, int q, double* partials, int nparts,
-                            int* err);
+// Read-only TMA pass: pair correlations of the index bits [a, a+5) and
+// [a2, a2+q-5) (a2 = a + 5: contiguous; 5 <= q <= 10), one partial per CTA in
+// partials[0 .. nparts).
+cudaError_t launch_corr_tma(const LaunchCtx& lc, const float2* psi, int n, int a, int a2, int q, double* partials,
+                            int nparts, int* err);
 
 // TMA-pipelined variants of the streaming passes (tma_kernels.cu).  err is a
 // device word set to nonzero when a bounded wait expires.  psi must be 16-byte

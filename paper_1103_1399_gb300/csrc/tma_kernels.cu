@@ -519,8 +519,8 @@ __device__ __forceinline__ unsigned long long pair_fma(const float2 (&v)[32], in
 
 template <int Q, int C>
 __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ? 1 : 3))
-    corr_tma_kernel(const __grid_constant__ CUtensorMap tmap, int a1, long long ntiles, double* __restrict__ partials,
-                    int nparts, int* __restrict__ err) {
+    corr_tma_kernel(const __grid_constant__ CUtensorMap tmap, int a1, int a2, long long ntiles,
+                    double* __restrict__ partials, int nparts, int* __restrict__ err) {
   using G = TmaGeom<Q, C>;
   constexpr int QB = Q - 5;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -530,12 +530,14 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
   const int tid = threadIdx.x;
   const int j = tid & ((1 << C) - 1);
   const int th = tid >> C;
-  const int lo_bits = a1 - C;
-  const unsigned long long lo_mask = (1ull << lo_bits) - 1ull;
+  // tile index T -> (low, middle, high) fixed-bit fields, as sp_tma_kernel
+  const int lo_bits = a1 - C, mid_bits = a2 - a1 - 5;
+  const unsigned long long lo_mask = (1ull << lo_bits) - 1ull, mid_mask = (1ull << mid_bits) - 1ull;
   const long long stride_t = gridDim.x;
   auto issue = [&](unsigned long long T) {
     mbar_expect_tx(s_bar, G::TILE * 8u);
-    tma_load_5d(s_buf, &tmap, static_cast<int>((T & lo_mask) << C), 0, 0, 0, static_cast<int>(T >> lo_bits), s_bar);
+    tma_load_5d(s_buf, &tmap, static_cast<int>((T & lo_mask) << C), 0, static_cast<int>((T >> lo_bits) & mid_mask), 0,
+                static_cast<int>(T >> (lo_bits + mid_bits)), s_bar);
   };
   if (tid == 0) {
     mbar_init(s_bar, 1);
@@ -670,24 +672,25 @@ static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int 
   return cudaGetLastError();
 }
 
-// The correlation pass over bits [a, a+q) (contiguous, 5 <= q <= 10, a >= 10):
-// one partial per CTA in partials[0 .. nparts).  Tiles of 2^q rows x 2^C
-// contiguous amplitudes, C = max(10 - q, 3) as in the strided passes, so that
-// a tile has at least 2^10 amplitudes and a CTA at least one whole warp.
+// The correlation pass over the bits [a, a+5) and [a2, a2+q-5) (a2 = a + 5 for
+// a contiguous group; 5 <= q <= 10, a >= 10): one partial per CTA in
+// partials[0 .. nparts).  Tiles of 2^q rows x 2^C contiguous amplitudes,
+// C = max(10 - q, 3) as in the strided passes, so that a tile has at least
+// 2^10 amplitudes and a CTA at least one whole warp.
 template <int Q>
-static cudaError_t launch_corr_q(const LaunchCtx& lc, const float2* psi, int n, int a, double* partials, int nparts,
-                                 int* err) {
+static cudaError_t launch_corr_q(const LaunchCtx& lc, const float2* psi, int n, int a, int a2, double* partials,
+                                 int nparts, int* err) {
   constexpr int C = tma_c(Q);
   using G = TmaGeom<Q, C>;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   constexpr int QB = Q - 5;
-  if (a < C || a + Q > n) return cudaErrorInvalidValue;
+  if (a < C || a2 < a + 5 || a2 + QB > n || (a2 != a + 5 && QB < 5)) return cudaErrorInvalidValue;
   CUtensorMap map;
-  // dims (innermost first): bits [0,a), [a,a+5), one, [a+5,a+Q), [a+Q,n)
-  const cuuint64_t dims[5] = {1ull << a, 32ull, 1ull, 1ull << QB, 1ull << (n - a - Q)};
-  const cuuint64_t strides[4] = {(1ull << a) * 8ull, (1ull << (a + 5)) * 8ull, (1ull << (a + 5)) * 8ull,
-                                 (1ull << (a + Q)) * 8ull};
+  // dims (innermost first): bits [0,a), [a,a+5), [a+5,a2), [a2,a2+QB), [a2+QB,n)
+  const cuuint64_t dims[5] = {1ull << a, 32ull, 1ull << (a2 - a - 5), 1ull << QB, 1ull << (n - a2 - QB)};
+  const cuuint64_t strides[4] = {(1ull << a) * 8ull, (1ull << (a + 5)) * 8ull, (1ull << a2) * 8ull,
+                                 (1ull << (a2 + QB)) * 8ull};
   const cuuint32_t box[5] = {1u << C, 32u, 1u, 1u << QB, 1u};
   const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
   const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<float2*>(psi), dims, strides, box, estr,
@@ -700,19 +703,19 @@ static cudaError_t launch_corr_q(const LaunchCtx& lc, const float2* psi, int n, 
   if (e != cudaSuccess) return e;
   long long grid = nparts;
   if (grid > ntiles) grid = ntiles;
-  kern<<<static_cast<unsigned>(grid), G::NT, G::smem, lc.stream>>>(map, a, ntiles, partials, nparts, err);
+  kern<<<static_cast<unsigned>(grid), G::NT, G::smem, lc.stream>>>(map, a, a2, ntiles, partials, nparts, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_corr_tma(const LaunchCtx& lc, const float2* psi, int n, int a, int q, double* partials, int nparts,
-                            int* err) {
+cudaError_t launch_corr_tma(const LaunchCtx& lc, const float2* psi, int n, int a, int a2, int q, double* partials,
+                            int nparts, int* err) {
   switch (q) {
-    case 5: return launch_corr_q<5>(lc, psi, n, a, partials, nparts, err);
-    case 6: return launch_corr_q<6>(lc, psi, n, a, partials, nparts, err);
-    case 7: return launch_corr_q<7>(lc, psi, n, a, partials, nparts, err);
-    case 8: return launch_corr_q<8>(lc, psi, n, a, partials, nparts, err);
-    case 9: return launch_corr_q<9>(lc, psi, n, a, partials, nparts, err);
-    case 10: return launch_corr_q<10>(lc, psi, n, a, partials, nparts, err);
+    case 5: return launch_corr_q<5>(lc, psi, n, a, a2, partials, nparts, err);
+    case 6: return launch_corr_q<6>(lc, psi, n, a, a2, partials, nparts, err);
+    case 7: return launch_corr_q<7>(lc, psi, n, a, a2, partials, nparts, err);
+    case 8: return launch_corr_q<8>(lc, psi, n, a, a2, partials, nparts, err);
+    case 9: return launch_corr_q<9>(lc, psi, n, a, a2, partials, nparts, err);
+    case 10: return launch_corr_q<10>(lc, psi, n, a, a2, partials, nparts, err);
     default: return cudaErrorInvalidValue;
   }
 }

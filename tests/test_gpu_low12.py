@@ -112,3 +112,26 @@ def test_low12_is_an_autotune_candidate_beyond_l2(env):
         assert "low pass bits [0,10)" in descs[0], descs[0]  # the default keeps the 10-bit low pass
         assert sum("low pass bits [0,12)" in d for d in descs) == 1, descs
     assert not any("low pass bits [0,12)" in d for d in q.tune_candidates(30))
+
+
+def test_qubits_per_pass_that_leave_no_12_bit_split_fall_back_to_10(env, monkeypatch):
+    """QAA_LOW_BITS=12 with q = 5 at n = 20: the 8 bits above a 12-bit low pass
+    have no split into groups of 5..5 bits, so the plan keeps the 10-bit low
+    pass (two 5-bit groups) instead of producing 4-bit groups; the evolution
+    matches the oracle."""
+    q, torch = env
+    monkeypatch.setenv("QAA_LOW_BITS", "12")
+    n, T, K = 20, 2.0, 8
+    cl = satgen.planted_instance(n, 11)["clauses"]
+    e = oracle.violated_counts(n, cl)
+    ref = oracle.evolve_strang(n, cl, T, K, energies=e)
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    with q.Instance(n, cl) as inst:
+        inst.set_variant(3, 5)
+        d = inst.describe_plan()
+        assert "low pass bits [0,10)" in d and d.count("group bits") == 2, d
+        inst.init_uniform(psi)
+        inst.evolve(psi, T, K)
+        o = inst.observables(psi)
+    assert np.max(np.abs(psi.cpu().numpy().astype(np.complex128) - ref)) <= 1e-5
+    assert abs(o["ground_prob"] - oracle.success_prob(ref, e)) <= 1e-6

@@ -55,8 +55,13 @@ def assert_close(got, ref):
 
 def test_two_calls_in_a_row_match_the_handle_path(env):
     q, torch = env
+    # n = 17: correlation passes above bit 10; n = 12: the plain correlation
+    # kernel; n = 6: one partial tile (amplitudes beyond 2^n masked), no pass
+    # above bit 10; m = 0: no clause upload, every E(x) = 0
     cases = [(17, satgen.random_instance(17, 80, seed=21), 1),
-             (12, satgen.planted_instance(12, 3)["clauses"], 2)]
+             (12, satgen.planted_instance(12, 3)["clauses"], 2),
+             (6, satgen.random_instance(6, 9, seed=5), 3),
+             (12, [], 4)]
     for n, clauses, seed in cases:
         psi = random_state(torch, n, seed)
         with q.Instance(n, clauses) as inst:
