@@ -457,8 +457,8 @@ def _in_flight(res):
         peak = max(peak, cur)
         last = t
     return {"max_in_flight": peak, "mean_in_flight": area / busy if busy > 0 else None,
-            "what": "requests whose device intervals (stream events before the first copy and after the "
-                    "read-back) overlap"}
+            "what": "requests whose device intervals (device-timer stamps before the first copy and at the end "
+                    "of the observables) overlap"}
 
 
 def _lat(lat):

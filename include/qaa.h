@@ -24,8 +24,10 @@
  * the assignment with x_i = bit (i - 1) of x.
  *
  * Conventions for every entry point:
- *   - Return a qaa_status; no C++ exception ever crosses this boundary.  On a
- *     failure qaa_last_error() returns a message for the calling thread.
+ *   - Return a qaa_status (qaa_version, qaa_tune_candidates and
+ *     qaa_last_error return a version, a count and a message); no C++
+ *     exception ever crosses this boundary.  On a failure qaa_last_error()
+ *     returns a message for the calling thread.
  *   - Device pointers (psi, out_dev) are caller-owned CUDA device memory on the
  *     current device; the library never frees or keeps them after the call.
  *     psi must hold 2^n complex64 values; the evolution calls need it 16-byte
@@ -83,15 +85,15 @@ const char* qaa_last_error(void);
  * if the device tables cannot be allocated.  Repeated clauses are allowed and
  * count with multiplicity in E(x).
  */
-int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out);
+qaa_status qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out);
 
 /* Release the handle and its device tables.  NULL is accepted. */
-int qaa_destroy(qaa_handle h);
+qaa_status qaa_destroy(qaa_handle h);
 
 /* Bind a cudaStream_t (as void*) for all later work of this handle; NULL = default
  * stream.  Switching to a different stream first waits for the handle's work on
  * the old one (the handle's device tables are reused across calls). */
-int qaa_set_stream(qaa_handle h, void* cuda_stream);
+qaa_status qaa_set_stream(qaa_handle h, void* cuda_stream);
 
 /*
  * qaa_set_variant -- choose the Walsh-Hadamard implementation of the
@@ -123,7 +125,7 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream);
  * Returns QAA_E_ARG for an unknown kind, a q outside those ranges, or a q for
  * which the n - 10 strided bits have no split into groups of 5..q bits.
  */
-int qaa_set_variant(qaa_handle h, int wht_kind, int q);
+qaa_status qaa_set_variant(qaa_handle h, int wht_kind, int q);
 
 /*
  * qaa_autotune -- choose the pass plan of a streaming-size handle (n >= 15)
@@ -150,7 +152,7 @@ int qaa_set_variant(qaa_handle h, int wht_kind, int q);
  * butterfly order differs).  Synchronous.  For n <= 14 there is nothing to
  * tune (QAA_OK, report says so).  The paper has no counterpart.
  */
-int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* report, size_t len);
+qaa_status qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* report, size_t len);
 
 /* Number of stage-1 autotune candidates for n (0 for n <= 14), with their
  * descriptions one per line in buf (NULL allowed).  Needs no GPU. */
@@ -178,11 +180,11 @@ int qaa_tune_candidates(int n, char* buf, size_t len);
  * start other than 0 / 1 or a non-finite s.  The paper has no counterpart
  * (it evolves without computing the spectrum).
  */
-int qaa_lowest_eigenvalues(qaa_handle h, double s, int k, int max_iter, int start, uint64_t seed, double* evals,
+qaa_status qaa_lowest_eigenvalues(qaa_handle h, double s, int k, int max_iter, int start, uint64_t seed, double* evals,
                            int* found, int* iters);
 
 /* Forget every plan recorded by qaa_autotune in this process. */
-int qaa_forget_tuned_plans(void);
+qaa_status qaa_forget_tuned_plans(void);
 
 /*
  * qaa_set_launch_mode -- how qaa_evolve* issue the streaming passes (n >= 15;
@@ -202,10 +204,10 @@ int qaa_forget_tuned_plans(void);
  */
 #define QAA_LAUNCH_PASSES 0
 #define QAA_LAUNCH_GRAPH 1
-int qaa_set_launch_mode(qaa_handle h, int mode);
+qaa_status qaa_set_launch_mode(qaa_handle h, int mode);
 
 /* psi[x] = 2^(-n/2) for all x: the ground state of H_B (Sec. 2.1).  Asynchronous. */
-int qaa_init_uniform(qaa_handle h, void* psi);
+qaa_status qaa_init_uniform(qaa_handle h, void* psi);
 
 /*
  * qaa_evolve -- evolve psi in place from s = 0 to s = 1 over total time T with
@@ -224,7 +226,7 @@ int qaa_init_uniform(qaa_handle h, void* psi);
  * its starting value instead of drifting with the roundings (about 4e-6
  * after 3200 steps at n = 20).
  */
-int qaa_evolve(qaa_handle h, void* psi, double T, int64_t steps);
+qaa_status qaa_evolve(qaa_handle h, void* psi, double T, int64_t steps);
 
 /*
  * qaa_evolve_range -- only steps k0 <= k < k1 of the `steps`-step run of
@@ -233,7 +235,7 @@ int qaa_evolve(qaa_handle h, void* psi, double T, int64_t steps);
  * floating-point rounding: this is checkpoint / resume (psi plus k is the
  * whole state of a run).  k0 == k1 is a no-op.
  */
-int qaa_evolve_range(qaa_handle h, void* psi, double T, int64_t steps, int64_t k0, int64_t k1);
+qaa_status qaa_evolve_range(qaa_handle h, void* psi, double T, int64_t steps, int64_t k0, int64_t k1);
 
 /*
  * qaa_evolve_schedule -- general schedule: `steps` Strang steps of length dt,
@@ -241,7 +243,7 @@ int qaa_evolve_range(qaa_handle h, void* psi, double T, int64_t steps, int64_t k
  * real range; 0..1 for the interpolation of Eq. (1)).  Used for non-linear
  * sweeps and for frozen-s closed-form checks.
  */
-int qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_values, int64_t steps);
+qaa_status qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_values, int64_t steps);
 
 /*
  * qaa_evolve_substeps -- `count` Strang sub-steps of individual length:
@@ -252,7 +254,7 @@ int qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_valu
  * exactly qaa_evolve_schedule.  Asynchronous on the handle's stream.
  * QAA_E_ARG for null arrays, count < 1 or a non-finite entry.
  */
-int qaa_evolve_substeps(qaa_handle h, void* psi, const double* dt_values, const double* s_values, int64_t count);
+qaa_status qaa_evolve_substeps(qaa_handle h, void* psi, const double* dt_values, const double* s_values, int64_t count);
 
 /*
  * qaa_evolve_order4 -- the linear schedule s = t/T of Eq. (1) in `steps`
@@ -264,7 +266,7 @@ int qaa_evolve_substeps(qaa_handle h, void* psi, const double* dt_values, const 
  * higher-order alternative to the Strang split of qaa_evolve).
  * QAA_E_ARG for T < 0 or not finite, steps outside [1, 2^28].
  */
-int qaa_evolve_order4(qaa_handle h, void* psi, double T, int64_t steps);
+qaa_status qaa_evolve_order4(qaa_handle h, void* psi, double T, int64_t steps);
 
 /*
  * Observables, accumulated in FP64 from the complex64 state with a fixed
@@ -283,23 +285,23 @@ typedef struct {
   int64_t ground_count;
 } qaa_obs;
 
-int qaa_observables(qaa_handle h, const void* psi, qaa_obs* out);
+qaa_status qaa_observables(qaa_handle h, const void* psi, qaa_obs* out);
 
 /* <H(s)> = (1 - s) <H_B> + s <H_P> of Eq. (1), FP64, synchronous. */
-int qaa_energy(qaa_handle h, const void* psi, double s, double* out);
+qaa_status qaa_energy(qaa_handle h, const void* psi, double s, double* out);
 
 /* Ground-state probability sum_{E(x)=0} |psi_x|^2, FP64, synchronous. */
-int qaa_success_prob(qaa_handle h, const void* psi, double* out);
+qaa_status qaa_success_prob(qaa_handle h, const void* psi, double* out);
 
 /* sum_x |psi_x|^2, FP64, synchronous. */
-int qaa_norm(qaa_handle h, const void* psi, double* out);
+qaa_status qaa_norm(qaa_handle h, const void* psi, double* out);
 
 /*
  * qaa_hp_diagonal -- write E(x) for every x (2^n uint16 values, caller-owned
  * device memory, 2-byte aligned) using the same in-kernel clause evaluation as
  * the evolution.  Exposed for bit-exact checks.  Asynchronous.
  */
-int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev);
+qaa_status qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev);
 
 /*
  * qaa_describe_plan -- write a one-line, NUL-terminated description of how this
@@ -308,7 +310,7 @@ int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev);
  * truncated to fit).  Host only; no CUDA work.  A library addition: the paper
  * has no counterpart.
  */
-int qaa_describe_plan(qaa_handle h, char* buf, size_t len);
+qaa_status qaa_describe_plan(qaa_handle h, char* buf, size_t len);
 
 /*
  * qaa_observables_noalloc -- the same five observables as qaa_observables,
@@ -342,7 +344,7 @@ int qaa_describe_plan(qaa_handle h, char* buf, size_t len);
  * must be serialised by the caller.
  */
 #define QAA_NOALLOC_MAX_PARTIALS 8192
-int qaa_observables_noalloc(int n, const int32_t* clauses, int m, const void* psi, void* cuda_stream,
+qaa_status qaa_observables_noalloc(int n, const int32_t* clauses, int m, const void* psi, void* cuda_stream,
                             qaa_obs* out);
 
 /*
@@ -368,11 +370,12 @@ typedef struct {
   double t_submit;       /* seconds on the server's steady clock                   */
   double t_admit;        /* memory granted (-1 if never admitted)                  */
   double t_done;         /* results available                                      */
-  double t_dev_start;    /* the request's device interval, seconds on the device   */
-  double t_dev_end;      /* clock since the server's creation (-1 if not run): from */
-                         /* an event before its first copy or kernel to one after  */
-                         /* its observables' read-back, on the stream it ran on;   */
-                         /* overlapping intervals = requests in flight together    */
+  double t_dev_start;    /* the request's device interval, seconds on the device's */
+  double t_dev_end;      /* global timer since the server's creation (-1 if not    */
+                         /* run): from a stamp before its first copy or kernel     */
+                         /* (batched requests: the start of their CTA) to the end  */
+                         /* of its observables' last kernel, on the stream it ran  */
+                         /* on; overlapping intervals = requests in flight together */
   int n;
   int64_t steps;
   int status;            /* QAA_OK, QAA_E_STATE (cancelled), QAA_E_CUDA, QAA_E_TIMEOUT */
@@ -388,16 +391,16 @@ typedef struct {
 
 /* hbm_budget_bytes: arena size (0 = free memory minus 4 GiB, at most 64 GiB);
  * max_slots: requests admitted at once (1..65536).  Starts the worker threads. */
-int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out);
+qaa_status qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out);
 /* Copies the instance (as qaa_create) and returns a ticket at once.  QAA_E_NOMEM
  * if the request can never fit in the arena; QAA_E_ARG for invalid input. */
-int qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, int64_t steps, uint64_t* ticket);
+qaa_status qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, int64_t steps, uint64_t* ticket);
 /* QAA_PENDING until done, then QAA_OK with *out filled (its status field tells
  * how the request ended).  Results stay available until the server is destroyed. */
-int qaa_poll(qaa_server* s, uint64_t ticket, qaa_result* out);
+qaa_status qaa_poll(qaa_server* s, uint64_t ticket, qaa_result* out);
 /* Cancel a request not yet admitted (QAA_E_STATE once admitted). */
-int qaa_cancel(qaa_server* s, uint64_t ticket);
-int qaa_server_stats(qaa_server* s, qaa_server_info* out);
+qaa_status qaa_cancel(qaa_server* s, uint64_t ticket);
+qaa_status qaa_server_stats(qaa_server* s, qaa_server_info* out);
 /* Fault injection for tests: fault 1 delays the worker thread by param
  * milliseconds once; fault 2 fails the next admitted request (status
  * QAA_E_CUDA) without touching the device; fault 3 starts the next persistent
@@ -405,9 +408,9 @@ int qaa_server_stats(qaa_server* s, qaa_server_info* out);
  * complete: its CTAs give up after the barrier's bounded wait (about a second),
  * record the error and return, and the request ends with QAA_E_TIMEOUT while
  * the server and the device stay usable.  No fault traps or faults the GPU. */
-int qaa_server_inject(qaa_server* s, int fault, int param);
+qaa_status qaa_server_inject(qaa_server* s, int fault, int param);
 /* Finishes running requests, cancels queued ones, releases everything. */
-int qaa_server_destroy(qaa_server* s);
+qaa_status qaa_server_destroy(qaa_server* s);
 
 /*
  * Launch profiling (tracing).  When enabled, the handle records a pair of CUDA
@@ -432,10 +435,10 @@ typedef enum {
   QAA_K_COUNT = 11
 } qaa_kernel_kind;
 
-int qaa_profile_enable(qaa_handle h, int on);
-int qaa_profile_reset(qaa_handle h);
+qaa_status qaa_profile_enable(qaa_handle h, int on);
+qaa_status qaa_profile_reset(qaa_handle h);
 /* kind in [0, QAA_K_COUNT); launches and total_ms may be NULL.  Synchronous. */
-int qaa_profile_read(qaa_handle h, int kind, int64_t* launches, double* total_ms);
+qaa_status qaa_profile_read(qaa_handle h, int kind, int64_t* launches, double* total_ms);
 
 #ifdef __cplusplus
 }

@@ -239,6 +239,13 @@ __device__ __forceinline__ void energies(int (&e)[32], const uint2* __restrict__
 }
 
 
+// The device's global nanosecond timer (the PTX special register %globaltimer).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // ---- norm fold (see NormFold) ------------------------------------------------
 // Sum of |v|^2 over a lane's 32 register-held amplitudes: packed FP32 FMAs in
 // two interleaved chains of 16, then one FP32 add per component.
@@ -254,67 +261,119 @@ __device__ __forceinline__ float tile_norm(const float2 (&v)[32]) {
   return (fa.x + fb.x) + (fa.y + fb.y);
 }
 
-// The correction factor of a low pass (1 when there is nothing to correct, or
-// when either sum is not a positive finite number), valid in lane 0.  One
-// whole warp calls it: lane i adds partials i, i + 32, ... of both slots (the
-// loads of the two slots in flight together; L2 loads, since within a
-// persistent kernel the slots were written by other CTAs since this SM last
-// read them), then a shuffle tree in the same fixed order in every CTA; only
-// lane 0 does the scalar FP64 work (GB300's FP64 rate is a small fraction of
-// its FP32 rate).
-__device__ __forceinline__ double fold_factor(const NormFold& f, int lane) {
-  if (!f.ref || !f.prev) return 1.0;
-  const int cr = static_cast<int>(__ldcg(f.ref)), cp = static_cast<int>(__ldcg(f.prev));
+// Double-float sums for the norm fold: hi + lo with |lo| <= ulp(hi) / 2.
+// df_add: Knuth's TwoSum of the leading parts, the trailing parts added to its
+// error, then renormalised (about 44 significant bits for sums of positive
+// terms); df_add1 adds one FP32 value.  No FMA contraction can apply (no
+// products), and nvcc does not reassociate FP32 additions.
+struct DFloat {
+  float hi, lo;
+};
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  const float t = e + (a.lo + b.lo);
+  const float h = s + t;
+  return DFloat{h, t - (h - s)};
+}
+__device__ __forceinline__ DFloat df_add1(DFloat a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  const float t = ((a.hi - (s - bb)) + (b - bb)) + a.lo;
+  const float h = s + t;
+  return DFloat{h, t - (h - s)};
+}
+__device__ __forceinline__ DFloat df_shfl_xor(DFloat a, int o) {
+  return DFloat{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+// c = sqrt(r / (s 2^k)), 2^k the power of two that brings s within a factor
+// sqrt(2) of r (1 when either is not a positive finite normal number).  The
+// scaling by 2^k is exact, r - s 2^k is exact in its leading part (Sterbenz:
+// the two are within a factor 2), and with eps = (r - s 2^k) / (s 2^k),
+// c = 1 + eps/2 - eps^2/8 to within eps^3 / 16 (1e-18 at the eps ~ 1e-6 of a
+// fold; sqrtf beyond |eps| = 0.01).
+__device__ __forceinline__ float fold_scale(DFloat r, DFloat s) {
+  const int er = (__float_as_int(r.hi) >> 23) & 0xff, es = (__float_as_int(s.hi) >> 23) & 0xff;
+  if (!(r.hi > 0.f) || !(s.hi > 0.f) || er == 0 || es == 0 || er == 0xff || es == 0xff) return 1.0f;
+  const int k = er - es;
+  if (k > 126 || k < -126) return 1.0f;
+  const float p = __int_as_float((127 + k) << 23);
+  float sh = s.hi * p, sl = s.lo * p;
+  if (sh > r.hi * 1.41421356f) {
+    sh *= 0.5f;
+    sl *= 0.5f;
+  } else if (sh < r.hi * 0.70710678f) {
+    sh *= 2.0f;
+    sl *= 2.0f;
+  }
+  const float eps = ((r.hi - sh) + (r.lo - sl)) / sh;
+  return fabsf(eps) < 1e-2f ? 1.0f + eps * (0.5f - 0.125f * eps) : sqrtf(1.0f + eps);
+}
+
+// The correction factor of a low pass (1 when there is nothing to correct),
+// valid in lane 0.  One whole warp calls it: lane i adds partials i, i + 32,
+// ... of both slots (the loads of the two slots in flight together; L2 loads,
+// since within a persistent kernel the slots were written by other CTAs since
+// this SM last read them), then a shuffle tree in the same fixed order in
+// every CTA.
+__device__ __forceinline__ float fold_factor(const NormFold& f, int lane) {
+  if (!f.ref || !f.prev) return 1.0f;
+  const int cr = __float_as_int(__ldcg(&f.ref[0].x)), cp = __float_as_int(__ldcg(&f.prev[0].x));
   const int cnt = cr > cp ? cr : cp;
-  double r = 0.0, s = 0.0;
+  DFloat r{0.f, 0.f}, s{0.f, 0.f};
   for (int i = lane; i < cnt; i += 32) {
-    if (i < cr) r += __ldcg(f.ref + 1 + i);
-    if (i < cp) s += __ldcg(f.prev + 1 + i);
+    if (i < cr) {
+      const float2 a = __ldcg(f.ref + 1 + i);
+      r = df_add(r, DFloat{a.x, a.y});
+    }
+    if (i < cp) {
+      const float2 b = __ldcg(f.prev + 1 + i);
+      s = df_add(s, DFloat{b.x, b.y});
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    r += __shfl_xor_sync(0xffffffffu, r, o);
-    s += __shfl_xor_sync(0xffffffffu, s, o);
+    r = df_add(r, df_shfl_xor(r, o));
+    s = df_add(s, df_shfl_xor(s, o));
   }
-  if (lane != 0) return 1.0;
-  if (!(r > 0.0) || !(s > 0.0) || !isfinite(r) || !isfinite(s)) return 1.0;
-  const double q = r / s;
-  const int j = static_cast<int>(rint(-log2(q)));  // N / N_ref ~ 2^j
-  return sqrt(ldexp(q, j));
+  return lane == 0 ? fold_scale(r, s) : 1.0f;
 }
 
 // Block-wide correction factor: warp 0 computes it, every thread gets it.
 // Contains a __syncthreads: every thread of the block must call it.
-__device__ __forceinline__ double fold_factor_block(const NormFold& f) {
-  __shared__ double s_c;
+__device__ __forceinline__ float fold_factor_block(const NormFold& f) {
+  __shared__ float s_c;
   if (threadIdx.x < 32) {
-    const double c = fold_factor(f, threadIdx.x);
+    const float c = fold_factor(f, threadIdx.x);
     if (threadIdx.x == 0) s_c = c;
   }
   __syncthreads();
   return s_c;
 }
 
-// Write the block's partial: the FP64 sum of one value per thread in a fixed
-// order; block 0 also writes the partial count.  Contains __syncthreads:
-// every thread of the block must call it.
-__device__ __forceinline__ void fold_store(const NormFold& f, double v) {
-  __shared__ double s_w[32];
+// Write the block's partial: the double-float sum of one pair per thread in a
+// fixed order; block 0 also writes the partial count.  Contains
+// __syncthreads: every thread of the block must call it.
+__device__ __forceinline__ void fold_store(const NormFold& f, DFloat v) {
+  __shared__ DFloat s_w[32];
   if (!f.out) return;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) s_w[warp] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += s_w[w];
-    f.out[1 + blockIdx.x] = t;
-    if (f.out2) f.out2[1 + blockIdx.x] = t;
+    DFloat t = s_w[0];
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) t = df_add(t, s_w[w]);
+    f.out[1 + blockIdx.x] = make_float2(t.hi, t.lo);
+    if (f.out2) f.out2[1 + blockIdx.x] = make_float2(t.hi, t.lo);
     if (blockIdx.x == 0) {
-      f.out[0] = static_cast<double>(gridDim.x);
-      if (f.out2) f.out2[0] = static_cast<double>(gridDim.x);
+      const float cnt = __int_as_float(static_cast<int>(gridDim.x));
+      f.out[0] = make_float2(cnt, 0.f);
+      if (f.out2) f.out2[0] = make_float2(cnt, 0.f);
     }
   }
 }

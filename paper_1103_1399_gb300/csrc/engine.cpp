@@ -20,9 +20,9 @@ namespace {
 
 thread_local std::string g_last_error = "no error";
 
-int fail(int code, const std::string& msg) {
+qaa_status fail(int code, const std::string& msg) {
   g_last_error = msg;
-  return code;
+  return static_cast<qaa_status>(code);
 }
 
 #define QAA_CK(expr)                                                                     \
@@ -127,7 +127,7 @@ cudaError_t timed(qaa_ctx* h, int kind, F&& launch) {
   return err;
 }
 
-int fold_profile(qaa_ctx* h) {
+qaa_status fold_profile(qaa_ctx* h) {
   if (h->pending.empty()) return QAA_OK;
   QAA_CK(cudaStreamSynchronize(h->stream));
   for (const auto& p : h->pending) {
@@ -145,7 +145,7 @@ int fold_profile(qaa_ctx* h) {
   return QAA_OK;
 }
 
-int ensure_tab(qaa_ctx* h, size_t entries) {
+qaa_status ensure_tab(qaa_ctx* h, size_t entries) {
   if (entries <= h->tab_cap) return QAA_OK;
   if (h->d_tab) {
     QAA_CK(cudaStreamSynchronize(h->stream));
@@ -161,14 +161,14 @@ int ensure_tab(qaa_ctx* h, size_t entries) {
   return QAA_OK;
 }
 
-int check_handle(qaa_ctx* h) {
+qaa_status check_handle(qaa_ctx* h) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   QAA_CK(cudaSetDevice(h->device));
   return QAA_OK;
 }
 
 // After a stream synchronisation: report (and clear) an expired device wait.
-int check_device_error(qaa_ctx* h) {
+qaa_status check_device_error(qaa_ctx* h) {
   int e = 0;
   QAA_CK(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (e != 0) {
@@ -217,7 +217,7 @@ const unsigned* stored_counts(qaa_ctx* h) {
 // Streaming plan, launch-graph mode: build (or reuse) the graph of the whole
 // range and launch it.  The graph is rebuilt when psi, the schedule, the range,
 // the variant or the stream changes.
-int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, long long k1, const double* s_dev,
+qaa_status evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, long long k1, const double* s_dev,
                  const double* dt_dev) {
   if (!h->d_gscratch) {
     if (cudaMalloc(&h->d_gscratch, qaa::graph_scratch_bytes(h->n, h->m)) != cudaSuccess) {
@@ -257,9 +257,9 @@ int evolve_graph(qaa_ctx* h, float2* psi, double dt, long long K, long long k0, 
 
 // s_host / dt_host (K entries each, optional): the caller's schedule and per-step
 // lengths, copied to the device ahead of the launches on the handle's stream.
-int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, long long k1, const double* s_host,
+qaa_status evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, long long k1, const double* s_host,
                 const double* dt_host = nullptr) {
-  int st = check_handle(h);
+  qaa_status st = check_handle(h);
   if (st) return st;
   if (!psi) return fail(QAA_E_ARG, "psi is null");
   if (reinterpret_cast<uintptr_t>(psi) % 16u) return fail(QAA_E_ARG, "psi must be 16-byte aligned");
@@ -326,8 +326,8 @@ int evolve_impl(qaa_ctx* h, void* psi, double dt, long long K, long long k0, lon
   return QAA_OK;
 }
 
-int observe(qaa_ctx* h, const void* psi, double out[5]) {
-  int st = check_handle(h);
+qaa_status observe(qaa_ctx* h, const void* psi, double out[5]) {
+  qaa_status st = check_handle(h);
   if (st) return st;
   if (!psi) return fail(QAA_E_ARG, "psi is null");
   if (reinterpret_cast<uintptr_t>(psi) % 8u) return fail(QAA_E_ARG, "psi must be 8-byte aligned");
@@ -367,7 +367,7 @@ int qaa_version(void) { return 1; }
 
 const char* qaa_last_error(void) { return g_last_error.c_str(); }
 
-int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out) {
+qaa_status qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out) {
   if (!out) return fail(QAA_E_ARG, "out is null");
   *out = nullptr;
   if (n < 1 || n > QAA_MAX_QUBITS) return fail(QAA_E_ARG, "n out of range [1, 34]");
@@ -413,7 +413,7 @@ int qaa_create(int n, const int32_t* clauses, int m, qaa_handle* out) {
   return QAA_OK;
 }
 
-int qaa_destroy(qaa_handle h) {
+qaa_status qaa_destroy(qaa_handle h) {
   if (!h) return QAA_OK;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -439,13 +439,13 @@ int qaa_destroy(qaa_handle h) {
   return QAA_OK;
 }
 
-int qaa_set_stream(qaa_handle h, void* cuda_stream) {
+qaa_status qaa_set_stream(qaa_handle h, void* cuda_stream) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   const cudaStream_t next = static_cast<cudaStream_t>(cuda_stream);
   if (next != h->stream) {
     // the handle's tables, counts and scratch are reused by the next call: the
     // old stream's work on them must be done before another stream touches them
-    int st = check_handle(h);
+    qaa_status st = check_handle(h);
     if (st) return st;
     QAA_CK(cudaStreamSynchronize(h->stream));
   }
@@ -453,7 +453,7 @@ int qaa_set_stream(qaa_handle h, void* cuda_stream) {
   return QAA_OK;
 }
 
-int qaa_set_variant(qaa_handle h, int wht_kind, int q) {
+qaa_status qaa_set_variant(qaa_handle h, int wht_kind, int q) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   if (wht_kind < 0 || wht_kind > 3)
     return fail(QAA_E_ARG, "unknown wht_kind (0 = FP32, 1 = BF16x3, 2 = BF16x2, 3 = rotation form)");
@@ -537,19 +537,19 @@ double time_plan(qaa_ctx* h, float2* psi, const qaa::PassPlan& plan, int steps, 
 
 }  // namespace
 
-int qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* report, size_t len) {
-  int st = check_handle(h);
+qaa_status qaa_autotune(qaa_handle h, void* psi, int steps, double budget_ms, char* report, size_t len) {
+  qaa_status st = check_handle(h);
   if (st) return st;
   if (!psi) return fail(QAA_E_ARG, "psi is null");
   if (reinterpret_cast<uintptr_t>(psi) % 16u) return fail(QAA_E_ARG, "psi must be 16-byte aligned");
   if (steps < 1 || steps > 64) return fail(QAA_E_ARG, "steps must be in [1, 64]");
   std::string rep;
-  auto finish = [&](int code) {
+  auto finish = [&](int code) -> qaa_status {
     if (report && len > 0) {
       std::strncpy(report, rep.c_str(), len - 1);
       report[len - 1] = '\0';
     }
-    return code;
+    return static_cast<qaa_status>(code);
   };
   if (h->n <= qaa::kOnchipMaxBits) {
     rep = "on-chip evolver: no pass plan to tune\n";
@@ -672,7 +672,7 @@ int qaa_tune_candidates(int n, char* buf, size_t len) {
   return static_cast<int>(cands.size());
 }
 
-int qaa_forget_tuned_plans(void) {
+qaa_status qaa_forget_tuned_plans(void) {
   qaa::clear_tuned_plans();
   return QAA_OK;
 }
@@ -717,9 +717,9 @@ std::vector<double> tridiag_eigs(const std::vector<double>& a, const std::vector
 
 }  // namespace
 
-int qaa_lowest_eigenvalues(qaa_handle h, double s, int k, int max_iter, int start, uint64_t seed, double* evals,
+qaa_status qaa_lowest_eigenvalues(qaa_handle h, double s, int k, int max_iter, int start, uint64_t seed, double* evals,
                            int* found, int* iters) {
-  int st = check_handle(h);
+  qaa_status st = check_handle(h);
   if (st) return st;
   if (!evals || !found) return fail(QAA_E_ARG, "evals or found is null");
   if (k < 1 || k > 8) return fail(QAA_E_ARG, "k must be in [1, 8]");
@@ -806,7 +806,7 @@ int qaa_lowest_eigenvalues(qaa_handle h, double s, int k, int max_iter, int star
   return check_device_error(h);
 }
 
-int qaa_set_launch_mode(qaa_handle h, int mode) {
+qaa_status qaa_set_launch_mode(qaa_handle h, int mode) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   if (mode != QAA_LAUNCH_PASSES && mode != QAA_LAUNCH_GRAPH)
     return fail(QAA_E_ARG, "unknown launch mode (0 = per-pass launches, 1 = launch graph)");
@@ -814,27 +814,27 @@ int qaa_set_launch_mode(qaa_handle h, int mode) {
   return QAA_OK;
 }
 
-int qaa_init_uniform(qaa_handle h, void* psi) {
-  int st = check_handle(h);
+qaa_status qaa_init_uniform(qaa_handle h, void* psi) {
+  qaa_status st = check_handle(h);
   if (st) return st;
   if (!psi) return fail(QAA_E_ARG, "psi is null");
   QAA_CK(timed(h, QAA_K_INIT, [&] { return qaa::launch_init_uniform(lctx(h), static_cast<float2*>(psi), h->n); }));
   return QAA_OK;
 }
 
-int qaa_evolve(qaa_handle h, void* psi, double T, int64_t steps) {
+qaa_status qaa_evolve(qaa_handle h, void* psi, double T, int64_t steps) {
   if (!(T >= 0.0) || !std::isfinite(T)) return fail(QAA_E_ARG, "T must be finite and >= 0");
   if (steps < 1) return fail(QAA_E_ARG, "steps must be >= 1");
   return evolve_impl(h, psi, T / static_cast<double>(steps), steps, 0, steps, nullptr);
 }
 
-int qaa_evolve_range(qaa_handle h, void* psi, double T, int64_t steps, int64_t k0, int64_t k1) {
+qaa_status qaa_evolve_range(qaa_handle h, void* psi, double T, int64_t steps, int64_t k0, int64_t k1) {
   if (!(T >= 0.0) || !std::isfinite(T)) return fail(QAA_E_ARG, "T must be finite and >= 0");
   if (steps < 1) return fail(QAA_E_ARG, "steps must be >= 1");
   return evolve_impl(h, psi, T / static_cast<double>(steps), steps, k0, k1, nullptr);
 }
 
-int qaa_evolve_substeps(qaa_handle h, void* psi, const double* dt_values, const double* s_values, int64_t count) {
+qaa_status qaa_evolve_substeps(qaa_handle h, void* psi, const double* dt_values, const double* s_values, int64_t count) {
   if (!dt_values || !s_values) return fail(QAA_E_ARG, "dt_values or s_values is null");
   if (count < 1) return fail(QAA_E_ARG, "count must be >= 1");
   for (int64_t k = 0; k < count; ++k)
@@ -843,7 +843,7 @@ int qaa_evolve_substeps(qaa_handle h, void* psi, const double* dt_values, const 
   return evolve_impl(h, psi, 0.0, count, 0, count, s_values, dt_values);
 }
 
-int qaa_evolve_order4(qaa_handle h, void* psi, double T, int64_t steps) {
+qaa_status qaa_evolve_order4(qaa_handle h, void* psi, double T, int64_t steps) {
   if (!(T >= 0.0) || !std::isfinite(T)) return fail(QAA_E_ARG, "T must be finite and >= 0");
   if (steps < 1 || steps > (1ll << 28)) return fail(QAA_E_ARG, "steps must be in [1, 2^28]");
   // Yoshida's triple jump: weights w1, w0, w1 with 2 w1 + w0 = 1, 2 w1^3 + w0^3 = 0
@@ -863,7 +863,7 @@ int qaa_evolve_order4(qaa_handle h, void* psi, double T, int64_t steps) {
   return evolve_impl(h, psi, 0.0, 3 * steps, 0, 3 * steps, ss.data(), dts.data());
 }
 
-int qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_values, int64_t steps) {
+qaa_status qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_values, int64_t steps) {
   if (!s_values) return fail(QAA_E_ARG, "s_values is null");
   if (steps < 1) return fail(QAA_E_ARG, "steps must be >= 1");
   for (int64_t k = 0; k < steps; ++k)
@@ -871,10 +871,10 @@ int qaa_evolve_schedule(qaa_handle h, void* psi, double dt, const double* s_valu
   return evolve_impl(h, psi, dt, steps, 0, steps, s_values);
 }
 
-int qaa_observables(qaa_handle h, const void* psi, qaa_obs* out) {
+qaa_status qaa_observables(qaa_handle h, const void* psi, qaa_obs* out) {
   if (!out) return fail(QAA_E_ARG, "out is null");
   double r[5];
-  int st = observe(h, psi, r);
+  qaa_status st = observe(h, psi, r);
   if (st) return st;
   out->norm = r[0];
   out->expect_hp = r[1];
@@ -884,35 +884,35 @@ int qaa_observables(qaa_handle h, const void* psi, qaa_obs* out) {
   return QAA_OK;
 }
 
-int qaa_energy(qaa_handle h, const void* psi, double s, double* out) {
+qaa_status qaa_energy(qaa_handle h, const void* psi, double s, double* out) {
   if (!out) return fail(QAA_E_ARG, "out is null");
   qaa_obs o;
-  int st = qaa_observables(h, psi, &o);
+  qaa_status st = qaa_observables(h, psi, &o);
   if (st) return st;
   *out = (1.0 - s) * o.expect_hb + s * o.expect_hp;
   return QAA_OK;
 }
 
-int qaa_success_prob(qaa_handle h, const void* psi, double* out) {
+qaa_status qaa_success_prob(qaa_handle h, const void* psi, double* out) {
   if (!out) return fail(QAA_E_ARG, "out is null");
   qaa_obs o;
-  int st = qaa_observables(h, psi, &o);
+  qaa_status st = qaa_observables(h, psi, &o);
   if (st) return st;
   *out = o.ground_prob;
   return QAA_OK;
 }
 
-int qaa_norm(qaa_handle h, const void* psi, double* out) {
+qaa_status qaa_norm(qaa_handle h, const void* psi, double* out) {
   if (!out) return fail(QAA_E_ARG, "out is null");
   qaa_obs o;
-  int st = qaa_observables(h, psi, &o);
+  qaa_status st = qaa_observables(h, psi, &o);
   if (st) return st;
   *out = o.norm;
   return QAA_OK;
 }
 
-int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev) {
-  int st = check_handle(h);
+qaa_status qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev) {
+  qaa_status st = check_handle(h);
   if (st) return st;
   if (!out_dev) return fail(QAA_E_ARG, "out is null");
   if (reinterpret_cast<uintptr_t>(out_dev) % 2u) return fail(QAA_E_ARG, "out must be 2-byte aligned");
@@ -920,7 +920,7 @@ int qaa_hp_diagonal(qaa_handle h, uint16_t* out_dev) {
   return QAA_OK;
 }
 
-int qaa_describe_plan(qaa_handle h, char* buf, size_t len) {
+qaa_status qaa_describe_plan(qaa_handle h, char* buf, size_t len) {
   if (!h) return fail(QAA_E_ARG, "null handle");
   if (!buf || len == 0) return fail(QAA_E_ARG, "buf is null or empty");
   const std::string d = qaa::describe_plan(h->plan);
@@ -929,8 +929,8 @@ int qaa_describe_plan(qaa_handle h, char* buf, size_t len) {
   return QAA_OK;
 }
 
-int qaa_profile_enable(qaa_handle h, int on) {
-  int st = check_handle(h);
+qaa_status qaa_profile_enable(qaa_handle h, int on) {
+  qaa_status st = check_handle(h);
   if (st) return st;
   if (!on) {
     st = fold_profile(h);
@@ -940,8 +940,8 @@ int qaa_profile_enable(qaa_handle h, int on) {
   return QAA_OK;
 }
 
-int qaa_profile_reset(qaa_handle h) {
-  int st = check_handle(h);
+qaa_status qaa_profile_reset(qaa_handle h) {
+  qaa_status st = check_handle(h);
   if (st) return st;
   st = fold_profile(h);
   if (st) return st;
@@ -952,8 +952,8 @@ int qaa_profile_reset(qaa_handle h) {
   return QAA_OK;
 }
 
-int qaa_profile_read(qaa_handle h, int kind, int64_t* launches, double* total_ms) {
-  int st = check_handle(h);
+qaa_status qaa_profile_read(qaa_handle h, int kind, int64_t* launches, double* total_ms) {
+  qaa_status st = check_handle(h);
   if (st) return st;
   if (kind < 0 || kind >= QAA_K_COUNT) return fail(QAA_E_ARG, "unknown kernel kind");
   st = fold_profile(h);

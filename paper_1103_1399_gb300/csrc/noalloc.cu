@@ -36,14 +36,14 @@ std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Messages go to the same thread-local slot that qaa_last_error() reports.
-int noalloc_fail(int code, const std::string& msg) {
+qaa_status noalloc_fail(int code, const std::string& msg) {
   qaa::set_last_error(msg);
-  return code;
+  return static_cast<qaa_status>(code);
 }
 
 }  // namespace
 
-extern "C" int qaa_observables_noalloc(int n, const int32_t* clauses, int m, const void* psi, void* cuda_stream,
+extern "C" qaa_status qaa_observables_noalloc(int n, const int32_t* clauses, int m, const void* psi, void* cuda_stream,
                                        qaa_obs* out) {
   if (!out) return noalloc_fail(QAA_E_ARG, "out is null");
   if (n < 1 || n > QAA_MAX_QUBITS) return noalloc_fail(QAA_E_ARG, "n out of range [1, 34]");

@@ -415,9 +415,11 @@ __global__ void __launch_bounds__(256)
 }
 
 // result[0..4] = norm, <H_P>, ground, count, C.  Regions 0..4 come from the low
-// kernel; regions 5.. are the strided correlation kernels (added to C).
+// kernel; regions 5.. are the strided correlation kernels (added to C).  With
+// stamp, the device time at the end (global_ns) is written there.
 __global__ void __launch_bounds__(256)
-    obs_reduce_kernel(const double* __restrict__ partials, int nparts, int nregions, double* __restrict__ result) {
+    obs_reduce_kernel(const double* __restrict__ partials, int nparts, int nregions, double* __restrict__ result,
+                      unsigned long long* __restrict__ stamp) {
   __shared__ double s[256];
   for (int q = 0; q < kObsQuant; ++q) {
     double t = 0.0;
@@ -434,6 +436,7 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x == 0) result[q] = s[0];
     __syncthreads();
   }
+  if (stamp && threadIdx.x == 0) *stamp = global_ns();
 }
 
 static int obs_grid(int num_sms) { return 2 * num_sms; }
@@ -489,7 +492,8 @@ cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, con
 }
 
 cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, int m, const ClauseLP* cl,
-                               double* partials, double* result, const unsigned* counts, int* err_word) {
+                               double* partials, double* result, const unsigned* counts, int* err_word,
+                               unsigned long long* stamp) {
   const int P = obs_grid(lc.num_sms);
   const long long ntiles = n > kLowBits ? (1ll << (n - kLowBits)) : 1ll;
   const bool stored = counts != nullptr && n > kLowBits;
@@ -521,7 +525,7 @@ cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, in
     }
     if (err != cudaSuccess) return err;
   }
-  obs_reduce_kernel<<<1, 256, 0, lc.stream>>>(partials, P, kObsQuant + cp.ng, result);
+  obs_reduce_kernel<<<1, 256, 0, lc.stream>>>(partials, P, kObsQuant + cp.ng, result, stamp);
   return cudaGetLastError();
 }
 

@@ -107,33 +107,26 @@ __device__ __forceinline__ void round_dispatch(float2* s_psi, const uint16_t* s_
 
 // The norm fold of a step (as in the streaming low passes): the block's sum of
 // one FP32 value per thread -- a fixed FP32 shuffle tree per warp, the warps'
-// sums added in FP64 by thread 0 -- and, with ref > 0, the factor that brings
-// it back to ref times the power of two nearest to sum / ref; without ref the
-// sum itself.  Thread 0 alone does the FP64 work (GB300's FP64 rate is a small
-// fraction of its FP32 rate) and every thread gets the result.
-__device__ double onchip_fold(float v, double ref) {
+// sums added as double-floats by thread 0 -- returned as a double-float pair
+// when ref is null, else the factor fold_scale(ref, sum) in .hi.  Every
+// thread gets the result.  Contains __syncthreads: every thread calls it.
+__device__ DFloat onchip_fold(float v, const DFloat* ref) {
   __shared__ float s_w[kOnchipThreads / 32];
-  __shared__ double s_out;
+  __shared__ DFloat s_out;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) s_w[warp] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += static_cast<double>(s_w[w]);
-    double out = t;
-    if (ref > 0.0) {
-      out = 1.0;
-      if (t > 0.0 && isfinite(t) && isfinite(ref)) {
-        const double q = ref / t;
-        out = sqrt(ldexp(q, static_cast<int>(rint(-log2(q)))));
-      }
-    }
-    s_out = out;
+    DFloat t{0.f, 0.f};
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t = df_add1(t, s_w[w]);
+    s_out = ref ? DFloat{fold_scale(*ref, t), 0.f} : t;
   }
   __syncthreads();
-  return s_out;
+  const DFloat out = s_out;
+  __syncthreads();  // s_out is written again by the next call
+  return out;
 }
 
 // Shared layout: [psi slots | E slots (uint16) | clauses], every region starting
@@ -170,7 +163,7 @@ __device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseM
     s_psi[oswz(x)] = a;
     racc += fmaf(a.x, a.x, a.y * a.y);  // at most 32 terms per thread (N <= 2^14)
   }
-  const double nref = onchip_fold(racc, 0.0);
+  const DFloat nref = onchip_fold(racc, nullptr);
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     int e = 0;
     for (int c = 0; c < m; ++c) {
@@ -205,7 +198,7 @@ __device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseM
       for (int g = G - 2; g >= 1; --g) round_dispatch(s_psi, s_e, n, g, kW1, p_first, brow, p_next, cs, &nacc);
       round_dispatch(s_psi, s_e, n, 0, kW1 | kPostP | (last ? 0u : kW3) | nrm, p_first, brow, p_next, cs, &nacc);
     }
-    cs = measure ? static_cast<float>(onchip_fold(nacc, nref > 0.0 ? nref : -1.0)) : 1.0f;
+    cs = measure ? onchip_fold(nacc, &nref).hi : 1.0f;
     w0_done = !last;
   }
   for (int x = threadIdx.x; x < N; x += blockDim.x) psi[x] = s_psi[oswz(x)];
@@ -223,6 +216,7 @@ __global__ void __launch_bounds__(kOnchipThreads) onchip_batch_kernel(const Onch
   extern __shared__ __align__(16) unsigned char smem[];
   if (static_cast<int>(blockIdx.x) >= njobs) return;
   const OnchipJob jb = jobs[blockIdx.x];
+  if (jb.stamp && threadIdx.x == 0) *jb.stamp = global_ns();
   onchip_run(jb.psi, jb.n, jb.m, jb.cl, jb.ptab, jb.btab, jb.nsteps, jb.first_p, smem, jb.init != 0, jb.init_val);
 }
 

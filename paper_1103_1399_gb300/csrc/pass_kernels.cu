@@ -69,12 +69,12 @@ __global__ void __launch_bounds__(kLpWarps * 32, 2)
   uint2* s_act = reinterpret_cast<uint2*>(smem + off + 8u * kLpTileSlots * kLpWarps) + warp * (m + 16);
 
   for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
-  const double fc = fold_factor_block(nf);  // norm correction of the previous step (1 if none)
+  const float fc = fold_factor_block(nf);  // norm correction of the previous step (1 if none)
   for (int i = threadIdx.x; i <= m; i += blockDim.x)
-    s_pt[i] = make_float2(static_cast<float>(prow[i].x * fc), static_cast<float>(prow[i].y * fc));
+    s_pt[i] = make_float2(prow[i].x * fc, prow[i].y * fc);
   __syncthreads();
 
-  double nacc = 0.0;
+  DFloat nacc{0.f, 0.f};
   const long long step = static_cast<long long>(gridDim.x) * kLpWarps;
   for (long long tile = static_cast<long long>(blockIdx.x) * kLpWarps + warp; tile < ntiles; tile += step) {
     float2* g = psi + (tile << kLowBits);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kLpWarps * 32, 2)
     }
 #pragma unroll
     for (int r = 0; r < 32; ++r) g[lane + 32 * r] = v[r];
-    if (nf.out) nacc += static_cast<double>(tile_norm(v));
+    if (nf.out) nacc = df_add1(nacc, tile_norm(v));
   }
   fold_store(nf, nacc);
 }
@@ -217,6 +217,8 @@ __global__ void __launch_bounds__(SpGeom<Q, C>::NT, (SpGeom<Q, C>::NT >= 256 ? 2
 }
 
 // ---------------------------------------------------------------------------
+__global__ void stamp_kernel(unsigned long long* __restrict__ stamp) { *stamp = global_ns(); }
+
 __global__ void init_uniform_kernel(float2* __restrict__ psi, unsigned long long count, float val) {
   const float2 z = make_float2(val, 0.0f);
   for (unsigned long long x = blockIdx.x * static_cast<unsigned long long>(blockDim.x) + threadIdx.x; x < count;
@@ -394,6 +396,11 @@ cudaError_t launch_pass(const LaunchCtx& lc, const Pass& p, float2* psi, int n, 
     }
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_stamp(const LaunchCtx& lc, unsigned long long* stamp) {
+  stamp_kernel<<<1, 1, 0, lc.stream>>>(stamp);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init_uniform(const LaunchCtx& lc, float2* psi, int n) {

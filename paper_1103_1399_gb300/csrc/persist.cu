@@ -94,8 +94,8 @@ __device__ void low_pass(const PersistArgs& A, const ClauseLP* s_cl, float2* s_t
   Pass fp{};
   fp.rel = rel;
   const NormFold nf = fold_for(A.fold, fp, fold_period(A.n));
-  const float fc = static_cast<float>(fold_factor_block(nf));
-  double nacc = 0.0;
+  const float fc = fold_factor_block(nf);
+  DFloat nacc{0.f, 0.f};
   for (long long tile = static_cast<long long>(blockIdx.x) * kPersistWarps + warp; tile < ntiles;
        tile += static_cast<long long>(gridDim.x) * kPersistWarps) {
     float2* g = A.psi + (tile << kLowBits);
@@ -128,7 +128,7 @@ __device__ void low_pass(const PersistArgs& A, const ClauseLP* s_cl, float2* s_t
     }
 #pragma unroll
     for (int r = 0; r < 32; ++r) g[lane + 32 * r] = v[r];
-    if (nf.out) nacc += static_cast<double>(tile_norm(v));
+    if (nf.out) nacc = df_add1(nacc, tile_norm(v));
   }
   fold_store(nf, nacc);
 }

@@ -76,8 +76,9 @@ struct Pass {
 // walk of roundings (about 4e-6 after 3200 Strang steps at 20 qubits, most of it
 // from the rounding of the few large amplitudes, so that the ground-state
 // probability drifts with it).  A low pass therefore also sums |psi|^2 of its
-// output (FP32 per 1024-amplitude tile, FP64 beyond, one partial per CTA), and
-// the next one multiplies its P row by
+// output (FP32 per 1024-amplitude tile, double-float FP32 pairs beyond -- an
+// FP32 sum and its exact rounding error -- one partial per CTA), and the next
+// one multiplies its P row by
 //   c = sqrt(N_ref 2^j / N),
 // N that sum, N_ref the sum taken by the first pass of the range and 2^j the
 // power of two nearest to N / N_ref (the unnormalised Walsh-Hadamard stages and
@@ -86,31 +87,39 @@ struct Pass {
 // the steps since the last one, so the corrections do not accumulate.  When
 // the state has concentrated on a few amplitudes the norm's error is mostly
 // theirs, so the correction also takes out most of their magnitude error.
-// Period F (fold_period): every step for n >= kFoldEveryStepBits, where the
-// extra reads are far below 1 % of a pass; every 8 steps below, where a pass
-// lasts microseconds (8: launch-graph bodies of 8 steps stay uniform).
-// Slots of kFoldSlot doubles: [0] = number of partials, then one per CTA.
-// Slot 0 holds the range's reference; F = 1 alternates slots 1 and 2 by step
-// parity (a pass reads one and writes the other), F = 8 uses slot 1.
+// Period F (fold_period): a fold costs a few microseconds per low pass (the
+// partials' reads and sums at its start, the per-tile sums, the block sum at
+// its end; 3.6 us per step measured at n = 22), and the norm drifts by about
+// 1e-7 per step from the phase tables' magnitude errors.  So F = 1 from
+// n = 26 (steps of 0.5 ms and more: under 1 %), 2 at n = 24..25, 4 at
+// n = 22..23 and 8 below, where steps last microseconds; F divides 8, so the
+// launch-graph bodies of 8 steps stay uniform.
+// Slots of kFoldSlot float pairs: [0].x = number of partials (integer bits),
+// then one (sum, error) pair per CTA.  Slot 0 holds the range's reference;
+// F = 1 alternates slots 1 and 2 by step parity (a pass reads one and writes
+// the other), F > 1 uses slot 1 (written by step r when F divides r + 1, read
+// by step r + 1).  All of it is FP32 arithmetic: GB300's FP64 rate is a small
+// fraction of its FP32 rate, and the scalar FP64 work of an earlier version
+// (sums, log2, sqrt on one thread) cost microseconds per pass.
 constexpr int kFoldSlot = 2048;
-constexpr int kFoldEveryStepBits = 22;
-constexpr size_t kFoldBytes = 3 * kFoldSlot * sizeof(double);
-__host__ __device__ inline int fold_period(int n) { return n >= kFoldEveryStepBits ? 1 : 8; }
+constexpr size_t kFoldBytes = 3 * kFoldSlot * sizeof(float2);
+__host__ __device__ inline int fold_period(int n) { return n >= 26 ? 1 : n >= 24 ? 2 : n >= 22 ? 4 : 8; }
 struct NormFold {
-  double* out = nullptr;         // slot this launch writes (null: none)
-  double* out2 = nullptr;        // a second slot written with the same partials
-  const double* ref = nullptr;   // the range's reference slot (null: no correction)
-  const double* prev = nullptr;  // the slot of the step to correct for
+  float2* out = nullptr;         // slot this launch writes (null: none)
+  float2* out2 = nullptr;        // a second slot written with the same partials
+  const float2* ref = nullptr;   // the range's reference slot (null: no correction)
+  const float2* prev = nullptr;  // the slot of the step to correct for
 };
 // Slots of a low pass with relative step p.rel and period F: the first pass
 // writes the reference and the slot step 0 reads (so that step 0's correction
 // is exactly 1); step r reads when r is a multiple of F and measures when
 // r + 1 is.
-__host__ __device__ inline NormFold fold_for(double* base, const Pass& p, int F) {
+__host__ __device__ inline NormFold fold_for(double* slots, const Pass& p, int F) {
   NormFold f;
-  if (!base || p.rel < -1) return f;
-  double* s1 = base + kFoldSlot;
-  double* s2 = base + 2 * kFoldSlot;
+  if (!slots || p.rel < -1) return f;
+  float2* base = reinterpret_cast<float2*>(slots);
+  float2* s1 = base + kFoldSlot;
+  float2* s2 = base + 2 * kFoldSlot;
   if (p.rel == -1) {
     f.out = base;
     f.out2 = F == 1 ? s2 : s1;
@@ -173,6 +182,7 @@ struct OnchipJob {
   int n, m, nsteps, first_p;
   int init;        // nonzero: start from the uniform superposition instead of reading psi
   float init_val;  // that amplitude, 2^(-n/2) rounded to FP32 on the host
+  unsigned long long* stamp;  // if not null: the device time at the job's start (global_ns)
 };
 cudaError_t launch_onchip_batch(const LaunchCtx& lc, const OnchipJob* jobs_dev, int njobs, size_t smem_bytes);
 cudaError_t launch_hp_diag(const LaunchCtx& lc, uint16_t* out, int n, int m, const ClauseLP* cl);
@@ -183,7 +193,11 @@ size_t obs_partials_len(int n, int num_sms);
 // err: the bounded-wait error word of the TMA correlation passes.
 cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, int m,
                                const ClauseLP* cl, double* partials, double* result,
-                               const unsigned* counts = nullptr, int* err = nullptr);
+                               const unsigned* counts = nullptr, int* err = nullptr,
+                               unsigned long long* stamp = nullptr);
+// One thread writes the device's nanosecond timer to *stamp (the start of a
+// served request's device interval; the observables' last kernel writes its end).
+cudaError_t launch_stamp(const LaunchCtx& lc, unsigned long long* stamp);
 // Read-only TMA pass: pair correlations of the index bits [a, a+5) and
 // [a2, a2+q-5) (a2 = a + 5: contiguous; 5 <= q <= 10), one partial per CTA in
 // partials[0 .. nparts).

@@ -41,9 +41,9 @@
 
 namespace {
 
-int sfail(int code, const std::string& msg) {
+qaa_status sfail(int code, const std::string& msg) {
   qaa::set_last_error(msg);
-  return code;
+  return static_cast<qaa_status>(code);
 }
 
 constexpr size_t kAlign = 256;
@@ -134,7 +134,6 @@ struct Req {
   size_t counts_bytes = 0;
   double* d_fold = nullptr;  // norm-fold slots of the low passes (streamed and persistent requests)
   cudaEvent_t done_ev = nullptr;
-  cudaEvent_t start_ev = nullptr;  // recorded before the request's first device work
   cudaGraphExec_t gexec = nullptr;  // launch graph of a streamed request, kept until it completes
   bool persist = false;  // mid-size: one persistent cooperative launch for the whole run
   bool graph = false;    // streamed: one launch graph for the whole run
@@ -176,10 +175,12 @@ struct qaa_server {
   char* arena_base = nullptr;
   Arena arena;
   std::vector<int> free_slots;
-  double* h_res = nullptr;  // pinned, 8 doubles per slot
+  // pinned, 8 doubles per slot: results [0..4], error word [5], the device
+  // interval's start and end stamps [6], [7] (global_ns of the device)
+  double* h_res = nullptr;
   unsigned char* h_stage = nullptr;  // pinned clause-table staging, kStageBytes per slot
   double t0 = 0;
-  cudaEvent_t ref_ev = nullptr;  // device-clock origin of the requests' device intervals
+  unsigned long long ref_ns = 0;  // device-clock origin of the requests' device intervals
   // submission (guarded by mu)
   std::mutex mu;
   std::condition_variable cv;
@@ -235,10 +236,6 @@ void release(qaa_server* s, Req* r) {
   if (r->done_ev) {
     cudaEventDestroy(r->done_ev);
     r->done_ev = nullptr;
-  }
-  if (r->start_ev) {
-    cudaEventDestroy(r->start_ev);
-    r->start_ev = nullptr;
   }
   if (r->gexec) {
     cudaGraphExecDestroy(r->gexec);
@@ -299,32 +296,40 @@ cudaError_t upload_tables(qaa_server* s, Req* r, cudaStream_t st) {
   return e;
 }
 
-// Observables of a finished evolution into the request's pinned slot, then
-// the completion event.
+// The request's device-interval stamps, in its result block after the five
+// results: [6] the start (global_ns before its first device work), [7] the end
+// (written by the observables' last kernel).
+unsigned long long* stamp_start(Req* r) { return reinterpret_cast<unsigned long long*>(r->d_res + 6); }
+unsigned long long* stamp_end(Req* r) { return reinterpret_cast<unsigned long long*>(r->d_res + 7); }
+
+// Observables of a finished evolution into the request's pinned slot (with
+// the device-interval stamps), then the completion event.
 cudaError_t observe_async(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
-  cudaError_t e = qaa::launch_observables(lc, r->psi, r->n, r->m, r->d_lp, r->d_part, r->d_res, r->d_counts, r->d_err);
+  cudaError_t e = qaa::launch_observables(lc, r->psi, r->n, r->m, r->d_lp, r->d_part, r->d_res, r->d_counts, r->d_err,
+                                          stamp_end(r));
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->h_res + 8 * r->slot, r->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(s->h_res + 8 * r->slot, r->d_res, 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_res + 8 * r->slot + 5, r->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaEventCreate(&r->done_ev);  // timed: the end of the request's device interval
+  // no timing: events with timing recorded on the persistent streams were
+  // measured to serialise their cooperative launches (half the throughput)
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(r->done_ev, st);
   return e;
 }
 
+// The start of a request's device interval: a stamp on its stream ahead of
+// its first copy or kernel.
+cudaError_t mark_start(qaa_server* s, Req* r, cudaStream_t st) {
+  return qaa::launch_stamp(qaa::LaunchCtx{st, s->num_sms}, stamp_start(r));
+}
+
 // The streaming evolution of one request (issuer thread, its own stream):
 // one launch graph for the whole run, or one launch per pass.
-// The start of a request's device interval: an event on its stream ahead of
-// its first copy or kernel.
-cudaError_t mark_start(Req* r, cudaStream_t st) {
-  cudaError_t e = cudaEventCreate(&r->start_ev);
-  if (e == cudaSuccess) e = cudaEventRecord(r->start_ev, st);
-  return e;
-}
 
 cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
-  cudaError_t e = mark_start(r, st);
+  cudaError_t e = mark_start(s, r, st);
   if (e == cudaSuccess) e = upload_tables(s, r, st);
   if (e == cudaSuccess) e = qaa::launch_init_uniform(lc, r->psi, r->n);
   if (e == cudaSuccess && r->d_counts) e = qaa::launch_lp_counts(lc, r->d_counts, r->n, r->m, r->d_lp);
@@ -371,7 +376,7 @@ cudaError_t issue_streaming(qaa_server* s, Req* r, cudaStream_t st) {
 // launch on a few CTAs, so several such requests share the GPU at once.
 cudaError_t issue_persistent(qaa_server* s, Req* r, cudaStream_t st) {
   const qaa::LaunchCtx lc{st, s->num_sms};
-  cudaError_t e = mark_start(r, st);
+  cudaError_t e = mark_start(s, r, st);
   if (e == cudaSuccess) e = upload_tables(s, r, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(r->d_bar, 0, 2 * sizeof(unsigned), st);
   // injected fault: the arrival count starts at 2^32 - 1, so the first grid
@@ -439,8 +444,7 @@ bool launch_batch(qaa_server* s, std::vector<Req*>& small) {
   int nj = 0;
   cudaError_t e = cudaSuccess;
   for (Req* r : small) {
-    e = mark_start(r, s->batch_stream);
-    if (e == cudaSuccess) e = upload_tables(s, r, s->batch_stream);
+    e = upload_tables(s, r, s->batch_stream);
     const double dt = r->T / static_cast<double>(r->K);
     float2* ptab = r->d_tab;
     float2* btab = r->d_tab + static_cast<size_t>(r->K + 1) * (r->m + 1);
@@ -457,6 +461,7 @@ bool launch_batch(qaa_server* s, std::vector<Req*>& small) {
     j.first_p = 1;
     j.init = 1;
     j.init_val = static_cast<float>(std::exp2(-0.5 * r->n));
+    j.stamp = stamp_start(r);  // batched requests: the device interval starts with their CTA
     smem = std::max(smem, qaa::onchip_smem_bytes(r->n, r->m));
   }
   if (e == cudaSuccess)
@@ -577,13 +582,12 @@ void worker_main(qaa_server* s) {
       }
       std::lock_guard<std::mutex> lk(s->mu);
       if (r->status == QAA_PENDING) {
-        float a = 0.f, b = 0.f;
-        if (r->start_ev && r->done_ev && cudaEventElapsedTime(&a, s->ref_ev, r->start_ev) == cudaSuccess &&
-            cudaEventElapsedTime(&b, s->ref_ev, r->done_ev) == cudaSuccess) {
-          r->t_dev_start = 1e-3 * a;
-          r->t_dev_end = 1e-3 * b;
-        } else {
-          cudaGetLastError();
+        unsigned long long a = 0, b = 0;
+        std::memcpy(&a, s->h_res + 8 * r->slot + 6, sizeof(a));
+        std::memcpy(&b, s->h_res + 8 * r->slot + 7, sizeof(b));
+        if (a >= s->ref_ns && b >= a) {
+          r->t_dev_start = 1e-9 * static_cast<double>(a - s->ref_ns);
+          r->t_dev_end = 1e-9 * static_cast<double>(b - s->ref_ns);
         }
         std::memcpy(r->res, s->h_res + 8 * r->slot, 5 * sizeof(double));
         int err = 0;
@@ -602,7 +606,7 @@ void worker_main(qaa_server* s) {
 
 extern "C" {
 
-int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) {
+qaa_status qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) {
   if (!out) return sfail(QAA_E_ARG, "out is null");
   *out = nullptr;
   if (max_slots < 1 || max_slots > 65536) return sfail(QAA_E_ARG, "max_slots out of range [1, 65536]");
@@ -618,7 +622,6 @@ int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) 
       if (s->jobs_ev[t]) cudaEventDestroy(s->jobs_ev[t]);
     }
     if (s->batch_stream) cudaStreamDestroy(s->batch_stream);
-    if (s->ref_ev) cudaEventDestroy(s->ref_ev);
     for (cudaStream_t st : s->issue_streams) cudaStreamDestroy(st);
     for (cudaStream_t st : s->persist_streams) cudaStreamDestroy(st);
     cudaGetLastError();
@@ -680,11 +683,16 @@ int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) 
       return bail(QAA_E_CUDA, "cannot create streams");
     s->persist_streams.push_back(st);
   }
-  // the device clock's origin for the requests' device intervals: recorded
-  // (and complete) before any request is issued
-  if (cudaEventCreate(&s->ref_ev) != cudaSuccess || cudaEventRecord(s->ref_ev, s->batch_stream) != cudaSuccess ||
-      cudaEventSynchronize(s->ref_ev) != cudaSuccess)
-    return bail(QAA_E_CUDA, "cannot record the reference event");
+  // the device clock's origin for the requests' device intervals, taken
+  // before any request is issued (in the arena's first bytes, which no
+  // request holds yet)
+  {
+    unsigned long long* d_ref = reinterpret_cast<unsigned long long*>(s->arena_base);
+    if (qaa::launch_stamp(qaa::LaunchCtx{s->batch_stream, s->num_sms}, d_ref) != cudaSuccess ||
+        cudaMemcpyAsync(&s->ref_ns, d_ref, sizeof(s->ref_ns), cudaMemcpyDeviceToHost, s->batch_stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->batch_stream) != cudaSuccess)
+      return bail(QAA_E_CUDA, "cannot read the device clock");
+  }
   s->t0 = steady_now();
   for (int i = 0; i < nissuers; ++i) s->issuers.emplace_back(issuer_main, s, i);
   s->worker = std::thread(worker_main, s);
@@ -692,7 +700,7 @@ int qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server** out) 
   return QAA_OK;
 }
 
-int qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, int64_t steps, uint64_t* ticket) {
+qaa_status qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, int64_t steps, uint64_t* ticket) {
   if (!s || !ticket) return sfail(QAA_E_ARG, "null server or ticket");
   if (n < 1 || n > QAA_MAX_QUBITS) return sfail(QAA_E_ARG, "n out of range [1, 34]");
   if (m < 0 || m > QAA_MAX_CLAUSES) return sfail(QAA_E_ARG, "m out of range [0, 1023]");
@@ -755,7 +763,7 @@ int qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, double T, in
   return QAA_OK;
 }
 
-int qaa_poll(qaa_server* s, uint64_t ticket, qaa_result* out) {
+qaa_status qaa_poll(qaa_server* s, uint64_t ticket, qaa_result* out) {
   if (!s || !out) return sfail(QAA_E_ARG, "null server or result");
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->all.find(ticket);
@@ -778,7 +786,7 @@ int qaa_poll(qaa_server* s, uint64_t ticket, qaa_result* out) {
   return QAA_OK;
 }
 
-int qaa_cancel(qaa_server* s, uint64_t ticket) {
+qaa_status qaa_cancel(qaa_server* s, uint64_t ticket) {
   if (!s) return sfail(QAA_E_ARG, "null server");
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->all.find(ticket);
@@ -789,7 +797,7 @@ int qaa_cancel(qaa_server* s, uint64_t ticket) {
   return QAA_OK;
 }
 
-int qaa_server_stats(qaa_server* s, qaa_server_info* out) {
+qaa_status qaa_server_stats(qaa_server* s, qaa_server_info* out) {
   if (!s || !out) return sfail(QAA_E_ARG, "null server or info");
   std::lock_guard<std::mutex> lk(s->mu);
   out->arena_bytes = s->arena.size();
@@ -800,7 +808,7 @@ int qaa_server_stats(qaa_server* s, qaa_server_info* out) {
   return QAA_OK;
 }
 
-int qaa_server_inject(qaa_server* s, int fault, int param) {
+qaa_status qaa_server_inject(qaa_server* s, int fault, int param) {
   if (!s) return sfail(QAA_E_ARG, "null server");
   if (fault == 1) {
     s->inject_delay_ms = std::max(param, 0);
@@ -816,7 +824,7 @@ int qaa_server_inject(qaa_server* s, int fault, int param) {
   return QAA_OK;
 }
 
-int qaa_server_destroy(qaa_server* s) {
+qaa_status qaa_server_destroy(qaa_server* s) {
   if (!s) return QAA_OK;
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -841,7 +849,6 @@ int qaa_server_destroy(qaa_server* s) {
   }
   cudaStreamSynchronize(s->batch_stream);
   cudaStreamDestroy(s->batch_stream);
-  cudaEventDestroy(s->ref_ev);
   for (int t = 0; t < 2; ++t) {
     cudaFreeHost(s->h_jobs[t]);
     cudaFree(s->d_jobs[t]);
@@ -852,7 +859,6 @@ int qaa_server_destroy(qaa_server* s) {
   cudaFreeHost(s->h_stage);
   for (auto& kv : s->all) {
     if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
-    if (kv.second->start_ev) cudaEventDestroy(kv.second->start_ev);
     if (kv.second->gexec) cudaGraphExecDestroy(kv.second->gexec);
     delete kv.second;
   }

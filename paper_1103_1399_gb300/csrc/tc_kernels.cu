@@ -230,10 +230,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   }
   // phase rows: P (low passes; the norm fold of the previous step folded in), B (phase group)
-  const double fc = fold_factor_block(nf);
+  const float fc = fold_factor_block(nf);
   if (LOW) {
     for (int i = tid; i <= m; i += kTcThreads)
-      s_pt[i] = make_float2(static_cast<float>(prow[i].x * fc), static_cast<float>(prow[i].y * fc));
+      s_pt[i] = make_float2(prow[i].x * fc, prow[i].y * fc);
   }
   if (KIND == kSpWBW) {
     for (int i = tid; i <= n; i += kTcThreads) s_bt[i] = brow[i];
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   };
 
-  double nacc = 0.0;  // |psi|^2 of this thread's outputs (norm fold of the low passes)
+  DFloat nacc{0.f, 0.f};  // |psi|^2 of this thread's outputs (norm fold of the low passes)
   uint32_t mma_phase = 0;
   int it = 0;
   int pending = -1;  // strided: the iteration whose TMA load is in flight
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float t = 0.0f;
 #pragma unroll
             for (int k = 0; k < 32; ++k) t = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, t));
-            nacc += static_cast<double>(t);
+            nacc = df_add1(nacc, t);
           }
         } else {
 #pragma unroll

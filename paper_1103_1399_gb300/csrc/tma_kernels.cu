@@ -397,9 +397,12 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
   constexpr bool kRot = KIND == kLpRot || KIND == kLpRot12;
   constexpr bool kQuad = KIND == kLpRot12;
   // and every merged pass folds in the norm correction of the previous step
-  const double psc = (kRot ? ldexp(1.0, -n) : 1.0) * fold_factor_block(nf);
-  for (int i = threadIdx.x; i <= m; i += blockDim.x)
-    s_pt[i] = make_float2(static_cast<float>(prow[i].x * psc), static_cast<float>(prow[i].y * psc));
+  const float fc = fold_factor_block(nf);
+  const float psc = kRot ? fc * __int_as_float((127 - n) << 23) : fc;  // 2^-n exactly (n <= 34)
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) {
+    const float2 pv = prow[i];
+    s_pt[i] = make_float2(pv.x * psc, pv.y * psc);
+  }
   float2 rtab[6];
 #pragma unroll
   for (int p = 0; p < 6; ++p) rtab[p] = kRot ? brow[p] : make_float2(0.f, 0.f);
@@ -423,7 +426,7 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     }
   }
   int it = 0;
-  double nacc = 0.0;  // |psi|^2 of this lane's outputs (norm fold)
+  DFloat nacc{0.f, 0.f};  // |psi|^2 of this lane's outputs (norm fold)
   for (long long tile = first; tile < ntiles; tile += step, ++it) {
     const bool ok = mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u);
     // a quad leaves together (its four warps have the same tiles left)
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     float2* g = psi + (tile << kLowBits) + lane;
 #pragma unroll
     for (int r = 0; r < 32; ++r) g[32 * r] = v[r];
-    if (nf.out) nacc += static_cast<double>(tile_norm(v));
+    if (nf.out) nacc = df_add1(nacc, tile_norm(v));
     if (tn < ntiles) {
       if (stored) {
         load_counts(counts, tn, lane, pl, nconst);

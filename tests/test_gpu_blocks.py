@@ -1,5 +1,6 @@
 """Full-size parity on real 3-literal clauses: block-product instances at n = 30
-and n = 32 (8 and 32 GiB states), in the launch configuration bench.py times.
+and n = 32 (8 and 32 GiB states), in the launch configuration bench.py times,
+and at n = 33 and 34 (the largest states one GPU holds).
 
 The instance (satgen.block_instance) splits the variables into blocks by
 residue, x_v in block (v - 1) mod B, so every block has variables among the
@@ -219,6 +220,29 @@ def test_block_instance_n32(env):
             h.evolve(psi, DT * K32, K32)
             o = h.observables(psi)
         check_state(torch, psi, o, ref, sample_points(inst, N32, 5))
+    finally:
+        del psi
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [33, 34])
+def test_block_instance_largest_states(env, n):
+    """The largest states one GB300 holds: 2^33 and 2^34 amplitudes (64 and
+    128 GiB, plus 11 and 22 GiB of stored per-tile counts), three strided
+    groups and 4 HBM round trips per step, 40 steps of the benchmark's dt."""
+    q, torch = env
+    inst = satgen.block_instance(n, 3, 160, 180, seed=11 + n)
+    K = 40
+    ref = BlockReference(inst, DT * K, K)
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    try:
+        with q.Instance(n, inst["clauses"]) as h:
+            plan = h.describe_plan()
+            h.init_uniform(psi)
+            h.evolve(psi, DT * K, K)
+            o = h.observables(psi)
+        assert "rotation form" in plan and plan.count("group bits") == 3, plan
+        check_state(torch, psi, o, ref, sample_points(inst, n, 6))
     finally:
         del psi
         torch.cuda.empty_cache()

@@ -208,8 +208,8 @@ def overlapping_pairs(rs):
 
 def test_requests_overlap_on_the_device(env):
     """Requests admitted together are in flight on the GPU at the same time:
-    their device intervals (events on the request's own stream, before its
-    first copy and after its results' read-back, on the device clock) overlap
+    their device intervals (device-timer stamps on the request's own stream,
+    before its first copy and at the end of its observables) overlap
     -- mid-size requests run as persistent launches on disjoint SMs, larger
     ones interleave their passes on the issuer streams -- and each result is
     still the same, bit for bit, as the same request served alone."""
