@@ -167,19 +167,27 @@ __device__ __forceinline__ void count_active(const uint2* __restrict__ act, int 
   for (int k = 0; k < kPlanes - 4; ++k) pl[4 + k] = hi[k];
 }
 
-// Stored per-tile counts (layout Y: registers hold bits 0..4): for tile t and
-// lane l, word (t * kCountWords + b) * 32 + l holds bit plane b of the lane's 32
-// violated-clause counts (b < kPlanes), and word kPlanes the tile's constant
-// part.  E(x) never changes during a run, so the merged low passes (and the
-// observables) can read these instead of folding and counting the clauses again.
-constexpr int kCountWords = kPlanes + 1;
+// Stored per-tile counts (layout Y: registers hold bits 0..4).  E(x) never
+// changes during a run, so the merged low passes (and the observables) read
+// these instead of folding and counting the clauses again.  Layout, in 32-bit
+// words:
+//   [0] P, the number of bit planes stored: the bits of the largest count of
+//       active (non-constant) violated clauses over every amplitude, so that
+//       the planes above P are zero everywhere and not stored (P = 7 instead
+//       of kPlanes = 10 for the 30-qubit benchmark instance: 0.88 instead of
+//       1.375 bytes per amplitude for the low pass to read);
+//   [1] the word offset of the planes, a multiple of 32 (128-byte rows);
+//   [32 + t] the constant part of tile t (clauses violated on the whole tile);
+//   [planes + (t P + b) 32 + l] bit plane b < P of lane l's 32 counts in tile t.
+constexpr int kCountHeaderWords = 32;
 
 __device__ __forceinline__ void load_counts(const unsigned* __restrict__ counts, long long tile, int lane,
                                             unsigned (&pl)[kPlanes], int& nconst) {
-  const unsigned* c = counts + static_cast<size_t>(tile) * (kCountWords * 32) + lane;
+  const int P = static_cast<int>(__ldg(counts));
+  const unsigned* c = counts + __ldg(counts + 1) + static_cast<size_t>(tile) * (32 * P) + lane;
 #pragma unroll
-  for (int b = 0; b < kPlanes; ++b) pl[b] = __ldg(c + 32 * b);
-  nconst = static_cast<int>(__ldg(c + 32 * kPlanes));
+  for (int b = 0; b < kPlanes; ++b) pl[b] = b < P ? __ldg(c + 32 * b) : 0u;
+  nconst = static_cast<int>(__ldg(counts + kCountHeaderWords + tile));
 }
 
 // Counts of registers R and R+16 packed as (count_R) | (count_{R+16} << 16).
@@ -288,17 +296,20 @@ __device__ __forceinline__ DFloat df_shfl_xor(DFloat a, int o) {
   return DFloat{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
-// c = sqrt(r / (s 2^k)), 2^k the power of two that brings s within a factor
-// sqrt(2) of r (1 when either is not a positive finite normal number).  The
-// scaling by 2^k is exact, r - s 2^k is exact in its leading part (Sterbenz:
-// the two are within a factor 2), and with eps = (r - s 2^k) / (s 2^k),
-// c = 1 + eps/2 - eps^2/8 to within eps^3 / 16 (1e-18 at the eps ~ 1e-6 of a
-// fold; sqrtf beyond |eps| = 0.01).
+// d = c - 1 for c = sqrt(r / (s 2^k)), 2^k the power of two that brings s
+// within a factor sqrt(2) of r (0 when either is not a positive finite normal
+// number).  The scaling by 2^k is exact, r - s 2^k is exact in its leading
+// part (Sterbenz: the two are within a factor 2), and with
+// eps = (r - s 2^k) / (s 2^k), d = eps/2 - eps^2/8 to within eps^3 / 16 (1e-18
+// at the eps ~ 1e-6 of a fold; sqrtf beyond |eps| = 0.01).  Kept as c - 1, d
+// carries c to about 1e-13 (c itself rounded to FP32 would be off by up to
+// 6e-8, a systematic norm error of 1.2e-7); a value x is scaled by
+// fold_apply(x, d) = x + x d, one rounding.
 __device__ __forceinline__ float fold_scale(DFloat r, DFloat s) {
   const int er = (__float_as_int(r.hi) >> 23) & 0xff, es = (__float_as_int(s.hi) >> 23) & 0xff;
-  if (!(r.hi > 0.f) || !(s.hi > 0.f) || er == 0 || es == 0 || er == 0xff || es == 0xff) return 1.0f;
+  if (!(r.hi > 0.f) || !(s.hi > 0.f) || er == 0 || es == 0 || er == 0xff || es == 0xff) return 0.0f;
   const int k = er - es;
-  if (k > 126 || k < -126) return 1.0f;
+  if (k > 126 || k < -126) return 0.0f;
   const float p = __int_as_float((127 + k) << 23);
   float sh = s.hi * p, sl = s.lo * p;
   if (sh > r.hi * 1.41421356f) {
@@ -309,17 +320,19 @@ __device__ __forceinline__ float fold_scale(DFloat r, DFloat s) {
     sl *= 2.0f;
   }
   const float eps = ((r.hi - sh) + (r.lo - sl)) / sh;
-  return fabsf(eps) < 1e-2f ? 1.0f + eps * (0.5f - 0.125f * eps) : sqrtf(1.0f + eps);
+  return fabsf(eps) < 1e-2f ? eps * (0.5f - 0.125f * eps) : sqrtf(1.0f + eps) - 1.0f;
 }
+__device__ __forceinline__ float fold_apply(float x, float d) { return fmaf(x, d, x); }
+__device__ __forceinline__ float2 fold_apply(float2 x, float d) { return make_float2(fmaf(x.x, d, x.x), fmaf(x.y, d, x.y)); }
 
-// The correction factor of a low pass (1 when there is nothing to correct),
-// valid in lane 0.  One whole warp calls it: lane i adds partials i, i + 32,
+// The correction of a low pass as d = c - 1 (0 when there is nothing to
+// correct), valid in lane 0.  One whole warp calls it: lane i adds partials i, i + 32,
 // ... of both slots (the loads of the two slots in flight together; L2 loads,
 // since within a persistent kernel the slots were written by other CTAs since
 // this SM last read them), then a shuffle tree in the same fixed order in
 // every CTA.
 __device__ __forceinline__ float fold_factor(const NormFold& f, int lane) {
-  if (!f.ref || !f.prev) return 1.0f;
+  if (!f.ref || !f.prev) return 0.0f;
   const int cr = __float_as_int(__ldcg(&f.ref[0].x)), cp = __float_as_int(__ldcg(&f.prev[0].x));
   const int cnt = cr > cp ? cr : cp;
   DFloat r{0.f, 0.f}, s{0.f, 0.f};
@@ -338,10 +351,10 @@ __device__ __forceinline__ float fold_factor(const NormFold& f, int lane) {
     r = df_add(r, df_shfl_xor(r, o));
     s = df_add(s, df_shfl_xor(s, o));
   }
-  return lane == 0 ? fold_scale(r, s) : 1.0f;
+  return lane == 0 ? fold_scale(r, s) : 0.0f;
 }
 
-// Block-wide correction factor: warp 0 computes it, every thread gets it.
+// Block-wide correction d = c - 1: warp 0 computes it, every thread gets it.
 // Contains a __syncthreads: every thread of the block must call it.
 __device__ __forceinline__ float fold_factor_block(const NormFold& f) {
   __shared__ float s_c;

@@ -36,7 +36,7 @@ __device__ __forceinline__ void col_wht(float2 (&v)[1 << W]) {
 }
 
 // kNorm: add |psi|^2 of the round's outputs to *nacc (FP32: at most one column
-// per thread at n <= 14); cs scales the popcount phase (the norm fold of the
+// per thread at n <= 14); cs = c - 1 scales the popcount phase (the norm fold of the
 // previous step).
 template <int W>
 __device__ void onchip_round(float2* __restrict__ s_psi, const uint16_t* __restrict__ s_e, int n, int b0,
@@ -62,9 +62,9 @@ __device__ void onchip_round(float2* __restrict__ s_psi, const uint16_t* __restr
       const int pc = __popc(xb);
 #pragma unroll
       for (int r = 0; r < (1 << W); ++r) v[r] = cmul(v[r], brow[pc + __popc(r)]);
-      if (cs != 1.0f) {
+      if (cs != 0.0f) {
 #pragma unroll
-        for (int r = 0; r < (1 << W); ++r) v[r] = make_float2(v[r].x * cs, v[r].y * cs);
+        for (int r = 0; r < (1 << W); ++r) v[r] = fold_apply(v[r], cs);
       }
     }
     if (flags & kW2) col_wht<W>(v);
@@ -108,7 +108,7 @@ __device__ __forceinline__ void round_dispatch(float2* s_psi, const uint16_t* s_
 // The norm fold of a step (as in the streaming low passes): the block's sum of
 // one FP32 value per thread -- a fixed FP32 shuffle tree per warp, the warps'
 // sums added as double-floats by thread 0 -- returned as a double-float pair
-// when ref is null, else the factor fold_scale(ref, sum) in .hi.  Every
+// when ref is null, else the correction c - 1 = fold_scale(ref, sum) in .hi.  Every
 // thread gets the result.  Contains __syncthreads: every thread calls it.
 __device__ DFloat onchip_fold(float v, const DFloat* ref) {
   __shared__ float s_w[kOnchipThreads / 32];
@@ -177,7 +177,7 @@ __device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseM
   const int G = (n + 4) / 5;
   const int mp1 = m + 1;
   bool w0_done = false;
-  float cs = 1.0f;  // norm fold of the previous step, applied with the popcount phase
+  float cs = 0.0f;  // norm fold c - 1 of the previous step, applied with the popcount phase
   for (int j = 0; j < nsteps; ++j) {
     const float2* p_first = ptab;  // row 0, only when first_p and j == 0
     const float2* p_next = ptab + static_cast<size_t>(j + 1) * mp1;
@@ -198,7 +198,7 @@ __device__ void onchip_run(float2* __restrict__ psi, int n, int m, const ClauseM
       for (int g = G - 2; g >= 1; --g) round_dispatch(s_psi, s_e, n, g, kW1, p_first, brow, p_next, cs, &nacc);
       round_dispatch(s_psi, s_e, n, 0, kW1 | kPostP | (last ? 0u : kW3) | nrm, p_first, brow, p_next, cs, &nacc);
     }
-    cs = measure ? onchip_fold(nacc, &nref).hi : 1.0f;
+    cs = measure ? onchip_fold(nacc, &nref).hi : 0.0f;
     w0_done = !last;
   }
   for (int x = threadIdx.x; x < N; x += blockDim.x) psi[x] = s_psi[oswz(x)];

@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(kLpWarps * 32, 2)
   uint2* s_act = reinterpret_cast<uint2*>(smem + off + 8u * kLpTileSlots * kLpWarps) + warp * (m + 16);
 
   for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
-  const float fc = fold_factor_block(nf);  // norm correction of the previous step (1 if none)
+  const float fd = fold_factor_block(nf);  // norm correction c - 1 of the previous step (0 if none)
   for (int i = threadIdx.x; i <= m; i += blockDim.x)
-    s_pt[i] = make_float2(prow[i].x * fc, prow[i].y * fc);
+    s_pt[i] = fold_apply(prow[i], fd);
   __syncthreads();
 
   DFloat nacc{0.f, 0.f};

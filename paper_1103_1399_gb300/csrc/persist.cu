@@ -94,7 +94,7 @@ __device__ void low_pass(const PersistArgs& A, const ClauseLP* s_cl, float2* s_t
   Pass fp{};
   fp.rel = rel;
   const NormFold nf = fold_for(A.fold, fp, fold_period(A.n));
-  const float fc = fold_factor_block(nf);
+  const float fd = fold_factor_block(nf);
   DFloat nacc{0.f, 0.f};
   for (long long tile = static_cast<long long>(blockIdx.x) * kPersistWarps + warp; tile < ntiles;
        tile += static_cast<long long>(gridDim.x) * kPersistWarps) {
@@ -118,9 +118,9 @@ __device__ void low_pass(const PersistArgs& A, const ClauseLP* s_cl, float2* s_t
       x2y(v, s_tile, lane);
       reg_wht<0, 5>(v);
       apply_p_phase(v, pl, nconst, tab);
-      if (fc != 1.0f) {
+      if (fd != 0.0f) {
 #pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] = make_float2(v[r].x * fc, v[r].y * fc);
+        for (int r = 0; r < 32; ++r) v[r] = fold_apply(v[r], fd);
       }
       if (KIND == kLpMerge) reg_wht<0, 5>(v);
       y2x(v, s_tile, lane);

@@ -230,10 +230,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   }
   // phase rows: P (low passes; the norm fold of the previous step folded in), B (phase group)
-  const float fc = fold_factor_block(nf);
+  const float fd = fold_factor_block(nf);
   if (LOW) {
     for (int i = tid; i <= m; i += kTcThreads)
-      s_pt[i] = make_float2(prow[i].x * fc, prow[i].y * fc);
+      s_pt[i] = fold_apply(prow[i], fd);
   }
   if (KIND == kSpWBW) {
     for (int i = tid; i <= n; i += kTcThreads) s_bt[i] = brow[i];

@@ -317,7 +317,7 @@ __device__ __forceinline__ void xpose_y2x_t(float2 (&v)[32], float2* __restrict_
 // KIND kLpPhase / kLpRot / kLpRot12: the rotation form (P alone; the
 // rotations of bits 0..9, or 0..11 with warp quads, then 2^-n P), with B row
 // entries 0..5 = exp(-i theta p).
-// Stored per-tile counts: kCountWords / load_counts (device_common.cuh).
+// Stored per-tile counts: load_counts (device_common.cuh).
 
 // Warp quads (kLpRot12): warps 4k..4k+3 of a CTA sync on named barrier 1 + k
 // (immediate ids, so that only barriers 0..2 are reserved).
@@ -397,11 +397,11 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
   constexpr bool kRot = KIND == kLpRot || KIND == kLpRot12;
   constexpr bool kQuad = KIND == kLpRot12;
   // and every merged pass folds in the norm correction of the previous step
-  const float fc = fold_factor_block(nf);
-  const float psc = kRot ? fc * __int_as_float((127 - n) << 23) : fc;  // 2^-n exactly (n <= 34)
+  const float fd = fold_factor_block(nf);
+  const float psc = kRot ? __int_as_float((127 - n) << 23) : 1.0f;  // 2^-n exactly (n <= 34)
   for (int i = threadIdx.x; i <= m; i += blockDim.x) {
     const float2 pv = prow[i];
-    s_pt[i] = make_float2(pv.x * psc, pv.y * psc);
+    s_pt[i] = fold_apply(make_float2(pv.x * psc, pv.y * psc), fd);
   }
   float2 rtab[6];
 #pragma unroll
@@ -741,15 +741,24 @@ int tma_run_bytes(int q, int run_c) {
   return 8 << c;
 }
 
-// The stored counts of every tile (layout Y), computed once per instance.
+// The stored counts of every tile (layout Y), computed once per instance in
+// two launches of the same fold and count: MEASURE raises the header's plane
+// count P to the bits of the largest count any lane holds, then the second
+// launch stores P planes and the constant part of every tile.
+template <bool MEASURE>
 __global__ void __launch_bounds__(kLpTmaWarps * 32)
-    lp_counts_kernel(int m, const ClauseLP* __restrict__ cl, unsigned* __restrict__ counts, long long ntiles) {
+    lp_counts_kernel(int m, const ClauseLP* __restrict__ cl, unsigned* __restrict__ counts, long long ntiles,
+                     unsigned planes_off) {
   extern __shared__ __align__(16) unsigned char smem[];
   ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint2* s_act = reinterpret_cast<uint2*>(smem + 16u * m) + warp * (m + 16);
   for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
   __syncthreads();
+  const int P = MEASURE ? kPlanes : static_cast<int>(counts[0]);
+  unsigned* planes = counts + planes_off;
+  if (!MEASURE && blockIdx.x == 0 && threadIdx.x == 0) counts[1] = planes_off;
+  unsigned used = 0u;  // OR of every plane word this lane computed, by plane
   for (long long tile = static_cast<long long>(blockIdx.x) * kLpTmaWarps + warp; tile < ntiles;
        tile += static_cast<long long>(gridDim.x) * kLpTmaWarps) {
     int nconst, npad;
@@ -757,26 +766,48 @@ __global__ void __launch_bounds__(kLpTmaWarps * 32)
     __syncwarp();
     fold_tile<true>(s_cl, m, static_cast<unsigned>(tile), lane, s_act, nconst, npad);
     count_active(s_act, npad, 1u << lane, pl);
-    unsigned* c = counts + static_cast<size_t>(tile) * (kCountWords * 32) + lane;
+    if (MEASURE) {
 #pragma unroll
-    for (int b = 0; b < kPlanes; ++b) c[32 * b] = pl[b];
-    c[32 * kPlanes] = static_cast<unsigned>(nconst);
+      for (int b = 0; b < kPlanes; ++b) used |= pl[b] != 0u ? (1u << b) : 0u;
+    } else {
+      unsigned* c = planes + static_cast<size_t>(tile) * (32 * P) + lane;
+#pragma unroll
+      for (int b = 0; b < kPlanes; ++b)
+        if (b < P) c[32 * b] = pl[b];
+      if (lane == 0) counts[kCountHeaderWords + tile] = static_cast<unsigned>(nconst);
+    }
+  }
+  if (MEASURE) {
+    used = __reduce_or_sync(0xffffffffu, used);
+    if (lane == 0 && used != 0u) atomicMax(counts, static_cast<unsigned>(32 - __clz(used)));
   }
 }
 
+static long long counts_planes_offset(long long ntiles) {
+  return kCountHeaderWords + ((ntiles + 31) / 32) * 32;
+}
+
 size_t lp_counts_bytes(int n) {
-  return n > kLowBits ? (static_cast<size_t>(1) << (n - kLowBits)) * kCountWords * 32 * sizeof(unsigned) : 0;
+  if (n <= kLowBits) return 0;
+  const long long ntiles = 1ll << (n - kLowBits);
+  return static_cast<size_t>(counts_planes_offset(ntiles) + ntiles * 32 * kPlanes) * sizeof(unsigned);
 }
 
 cudaError_t launch_lp_counts(const LaunchCtx& lc, unsigned* counts, int n, int m, const ClauseLP* cl) {
   const long long ntiles = 1ll << (n - kLowBits);
   const size_t smem = 16u * static_cast<size_t>(m) + static_cast<size_t>(kLpTmaWarps) * 8u * (m + 16);
-  cudaError_t e = allow_smem(reinterpret_cast<const void*>(lp_counts_kernel),
-                             16u * QAA_MAX_CLAUSES_DEV + static_cast<size_t>(kLpTmaWarps) * 8u * (QAA_MAX_CLAUSES_DEV + 16));
+  const size_t smem_max = 16u * QAA_MAX_CLAUSES_DEV + static_cast<size_t>(kLpTmaWarps) * 8u * (QAA_MAX_CLAUSES_DEV + 16);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(lp_counts_kernel<true>), smem_max);
+  if (e == cudaSuccess) e = allow_smem(reinterpret_cast<const void*>(lp_counts_kernel<false>), smem_max);
   if (e != cudaSuccess) return e;
+  // the header's P is raised from 0 by the first launch; the second writes the planes' offset
+  e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned), lc.stream);
+  if (e != cudaSuccess) return e;
+  const unsigned off = static_cast<unsigned>(counts_planes_offset(ntiles));
   long long grid = (ntiles + kLpTmaWarps - 1) / kLpTmaWarps;
   if (grid > 4ll * lc.num_sms) grid = 4ll * lc.num_sms;
-  lp_counts_kernel<<<static_cast<unsigned>(grid), kLpTmaWarps * 32, smem, lc.stream>>>(m, cl, counts, ntiles);
+  lp_counts_kernel<true><<<static_cast<unsigned>(grid), kLpTmaWarps * 32, smem, lc.stream>>>(m, cl, counts, ntiles, off);
+  lp_counts_kernel<false><<<static_cast<unsigned>(grid), kLpTmaWarps * 32, smem, lc.stream>>>(m, cl, counts, ntiles, off);
   return cudaGetLastError();
 }
 
