@@ -19,7 +19,8 @@ variables all lie at bits >= 10 reach the constant part of a tile's count.
 Checked against the oracle: 4000 sampled amplitudes (plus the planted
 assignment and its complement) relative to the largest amplitude (REL_TOL, as
 the product-instance tests), the raw ground-state probability (1e-6), the norm
-(1e-6), the ground count (exact) and E(x) at the sampled points (bit exact),
+(1e-6), <H_B> and <H_P> (1e-5: sums of the blocks' values), the ground count
+(exact) and E(x) at the sampled points (bit exact),
 for the default plan (rotation form, stored per-tile counts), counting on the
 fly (QAA_LP_COUNTS=0), one launch graph, and the W.B.W form; and the n = 32
 planted benchmark instance's ground count, by the GPU's own E(x), equal to the
@@ -40,6 +41,7 @@ DT = 0.1
 REL_TOL = 1e-5
 PROB_TOL = 1e-6
 NORM_TOL = 1e-6
+EXP_TOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -89,6 +91,13 @@ class BlockReference:
     def ground_count(self):
         return int(np.prod([np.count_nonzero(e == 0) for _, e, _ in self.blocks]))
 
+    # <H_B> and <H_P> are sums over blocks (each block state has norm 1 to 1e-15)
+    def expect_hb(self):
+        return float(sum(oracle.expect_hb(len(blk["vars"]), psi) for blk, _, psi in self.blocks))
+
+    def expect_hp(self):
+        return float(sum(oracle.expect_hp(psi, e) for _, e, psi in self.blocks))
+
 
 def sample_points(inst, n, seed):
     rng = np.random.default_rng(seed)
@@ -110,6 +119,11 @@ def check_state(torch, psi, o, ref, xs, prob_tol=PROB_TOL):
     assert abs(dp) <= prob_tol, (o["ground_prob"], ref.ground_prob())
     assert abs(o["norm"] - 1.0) <= NORM_TOL, o["norm"]
     assert o["ground_count"] == ref.ground_count()
+    # the correlation passes (one chunked launch for two groups up to n = 30)
+    # and the energy sum, against the blocks' oracle values; the FP32 state's
+    # error bounds them, not the reductions
+    assert o["expect_hb"] == pytest.approx(ref.expect_hb(), rel=EXP_TOL, abs=EXP_TOL)
+    assert o["expect_hp"] == pytest.approx(ref.expect_hp(), rel=EXP_TOL, abs=EXP_TOL)
     return got
 
 

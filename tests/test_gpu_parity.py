@@ -238,7 +238,9 @@ def test_no_clauses_keeps_uniform(q, torch):
 
 
 # ---------------------------------------------------------------- observables
-@pytest.mark.parametrize("n", [1, 3, 10, 12, 17, 21])
+# n = 22 and 24: the two equal correlation groups (6 + 6, 7 + 7 bits) run as one
+# chunked launch
+@pytest.mark.parametrize("n", [1, 3, 10, 12, 17, 21, 22, 24])
 def test_observables_match_oracle(q, torch, n):
     cl = satgen.random_instance(n, 4 * n, seed=n, width=min(3, n))
     e = oracle.violated_counts(n, cl)
