@@ -441,10 +441,6 @@ __global__ void __launch_bounds__(256)
 
 static int obs_grid(int num_sms) { return 2 * num_sms; }
 
-// Largest n whose two correlation groups run as one chunked launch: a chunk
-// holds 2^(n - 10 + C) amplitudes, 64 MB at n = 30 (C = 3), half the L2.
-constexpr int kCorrFuseMaxBits = 30;
-
 // Correlation passes over bits [10, n): contiguous groups of 5..10 bits (as
 // even as possible) on the TMA tile passes, else groups of at most 5 bits with
 // plain loads (and always for n - 10 < 5).
@@ -518,15 +514,6 @@ cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, in
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   // the TMA passes need an error word for their bounded waits
   const CorrPlan cp = corr_plan(n, err_word != nullptr && reinterpret_cast<uintptr_t>(psi) % 16u == 0);
-  // two equal TMA groups up to n = 30: one launch, chunks of at most 64 MB in L2
-  // (at n = 30 the two passes took 2 x 1.34 ms)
-  if (cp.tma && cp.ng == 2 && cp.q[0] == cp.q[1] && n <= kCorrFuseMaxBits) {
-    err = launch_corr_tma(lc, psi, n, cp.a[0], cp.a2[0], cp.q[0], partials + static_cast<size_t>(kObsQuant) * P, P,
-                          err_word, cp.a[1], cp.a2[1]);
-    if (err != cudaSuccess) return err;
-    obs_reduce_kernel<<<1, 256, 0, lc.stream>>>(partials, P, kObsQuant + 1, result, stamp);
-    return cudaGetLastError();
-  }
   for (int k = 0; k < cp.ng; ++k) {
     double* part = partials + static_cast<size_t>(kObsQuant + k) * P;
     if (cp.tma) {

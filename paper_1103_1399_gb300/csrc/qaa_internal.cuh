@@ -200,11 +200,9 @@ cudaError_t launch_observables(const LaunchCtx& lc, const float2* psi, int n, in
 cudaError_t launch_stamp(const LaunchCtx& lc, unsigned long long* stamp);
 // Read-only TMA pass: pair correlations of the index bits [a, a+5) and
 // [a2, a2+q-5) (a2 = a + 5: contiguous; 5 <= q <= 10), one partial per CTA in
-// partials[0 .. nparts).  With b >= 0 the same launch adds a second q-bit
-// group [b, b+5) + [b2, b2+q-5), the two holding every bit of [10, n) once:
-// taken chunk by chunk so that the second group's tiles read the state from L2.
+// partials[0 .. nparts).
 cudaError_t launch_corr_tma(const LaunchCtx& lc, const float2* psi, int n, int a, int a2, int q, double* partials,
-                            int nparts, int* err, int b = -1, int b2 = -1);
+                            int nparts, int* err);
 
 // TMA-pipelined variants of the streaming passes (tma_kernels.cu).  err is a
 // device word set to nonzero when a bounded wait expires.  psi must be 16-byte

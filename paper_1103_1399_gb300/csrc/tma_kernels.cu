@@ -520,25 +520,10 @@ __device__ __forceinline__ unsigned long long pair_fma(const float2 (&v)[32], in
   return c;
 }
 
-// One launch can cover two groups that together hold every index bit from 10
-// up (two strided tile families, tensor maps tmap and tmap2): the work items
-// are taken chunk by chunk, where a chunk fixes the index bits [C, 10) and so
-// holds 2^(n - 10 + C) amplitudes (64 MB at n = 30, inside the 129 MB L2):
-// first the chunk's tiles of the first family, which read it from HBM, then
-// its tiles of the second, which find it in L2.  A family's tile index is then
-// chunk | (r << cbits), r enumerating the other family's bits in ascending
-// order (na and nb tiles per chunk; nb = 0 for one group).
-struct CorrWork {
-  int a1[2], a2[2];
-  int cbits;
-  long long na, nb;
-};
-
 template <int Q, int C>
 __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ? 1 : 3))
-    corr_tma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap2,
-                    const CorrWork cw, long long nwork, double* __restrict__ partials, int nparts,
-                    int* __restrict__ err) {
+    corr_tma_kernel(const __grid_constant__ CUtensorMap tmap, int a1, int a2, long long ntiles,
+                    double* __restrict__ partials, int nparts, int* __restrict__ err) {
   using G = TmaGeom<Q, C>;
   constexpr int QB = Q - 5;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -548,35 +533,27 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
   const int tid = threadIdx.x;
   const int j = tid & ((1 << C) - 1);
   const int th = tid >> C;
+  // tile index T -> (low, middle, high) fixed-bit fields, as sp_tma_kernel
+  const int lo_bits = a1 - C, mid_bits = a2 - a1 - 5;
+  const unsigned long long lo_mask = (1ull << lo_bits) - 1ull, mid_mask = (1ull << mid_bits) - 1ull;
   const long long stride_t = gridDim.x;
-  // work item -> family and its tile index T -> (low, middle, high) fixed-bit
-  // fields, as sp_tma_kernel
-  auto issue = [&](long long w) {
-    int f = 0;
-    unsigned long long T = static_cast<unsigned long long>(w);
-    if (cw.nb > 0) {
-      const long long per = cw.na + cw.nb, c = w / per, r = w % per;
-      f = r >= cw.na ? 1 : 0;
-      T = static_cast<unsigned long long>(c) | (static_cast<unsigned long long>(f ? r - cw.na : r) << cw.cbits);
-    }
-    const int lo_bits = cw.a1[f] - C, mid_bits = cw.a2[f] - cw.a1[f] - 5;
-    const unsigned long long lo_mask = (1ull << lo_bits) - 1ull, mid_mask = (1ull << mid_bits) - 1ull;
+  auto issue = [&](unsigned long long T) {
     mbar_expect_tx(s_bar, G::TILE * 8u);
-    tma_load_5d(s_buf, f ? &tmap2 : &tmap, static_cast<int>((T & lo_mask) << C), 0,
-                static_cast<int>((T >> lo_bits) & mid_mask), 0, static_cast<int>(T >> (lo_bits + mid_bits)), s_bar);
+    tma_load_5d(s_buf, &tmap, static_cast<int>((T & lo_mask) << C), 0, static_cast<int>((T >> lo_bits) & mid_mask), 0,
+                static_cast<int>(T >> (lo_bits + mid_bits)), s_bar);
   };
   if (tid == 0) {
     mbar_init(s_bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0 && static_cast<long long>(blockIdx.x) < nwork) issue(blockIdx.x);
+  if (tid == 0 && static_cast<long long>(blockIdx.x) < ntiles) issue(blockIdx.x);
   const int h_off = j + (th << C);
   const int sx_h = G::slot(j + (th << C));
   const int sx_l = j + (th << (C + 5)) + (th << C);
   double acc = 0.0;
   int it = 0;
-  for (long long w = blockIdx.x; w < nwork; w += stride_t, ++it) {
+  for (long long T = blockIdx.x; T < ntiles; T += stride_t, ++it) {
     const bool ok = mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicExch(err, kErrTimeout);
@@ -597,9 +574,9 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
       for (int r = 0; r < 32; ++r) v[r] = s_buf[sx_l + (r << C)];
     }
     __syncthreads();  // buffer free: the next tile's copy overlaps the rest of this one
-    if (tid == 0 && w + stride_t < nwork) {
+    if (tid == 0 && T + stride_t < ntiles) {
       fence_proxy_async();
-      issue(w + stride_t);
+      issue(static_cast<unsigned long long>(T + stride_t));
     }
 #pragma unroll
     for (int b = 0; b < 5; ++b)
@@ -608,8 +585,8 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
     acc += static_cast<double>(c.x + c.y);
   }
   if (tid == 0) {
-    const long long w = blockIdx.x + static_cast<long long>(it) * stride_t;
-    if (w < nwork && !mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u)) atomicExch(err, kErrTimeout);
+    const long long T = blockIdx.x + static_cast<long long>(it) * stride_t;
+    if (T < ntiles && !mbar_wait_bounded(s_bar, static_cast<uint32_t>(it) & 1u)) atomicExch(err, kErrTimeout);
   }
   // fixed-order block sum; CTAs beyond the grid's share write zero partials
 #pragma unroll
@@ -702,79 +679,46 @@ static cudaError_t launch_sp_tma_c(const LaunchCtx& lc, float2* psi, int n, int 
 // a contiguous group; 5 <= q <= 10, a >= 10): one partial per CTA in
 // partials[0 .. nparts).  Tiles of 2^q rows x 2^C contiguous amplitudes,
 // C = max(10 - q, 3) as in the strided passes, so that a tile has at least
-// 2^10 amplitudes and a CTA at least one whole warp.  With b >= 0, the same
-// launch also covers a second q-bit group [b, b+5) + [b2, b2+q-5); the two
-// groups must hold every bit of [10, n) once (chunked work, see CorrWork).
+// 2^10 amplitudes and a CTA at least one whole warp.
 template <int Q>
-static cudaError_t corr_map(const float2* psi, int n, int a, int a2, CUtensorMap* map) {
+static cudaError_t launch_corr_q(const LaunchCtx& lc, const float2* psi, int n, int a, int a2, double* partials,
+                                 int nparts, int* err) {
   constexpr int C = tma_c(Q);
-  constexpr int QB = Q - 5;
+  using G = TmaGeom<Q, C>;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
+  constexpr int QB = Q - 5;
   if (a < C || a2 < a + 5 || a2 + QB > n || (a2 != a + 5 && QB < 5)) return cudaErrorInvalidValue;
+  CUtensorMap map;
   // dims (innermost first): bits [0,a), [a,a+5), [a+5,a2), [a2,a2+QB), [a2+QB,n)
   const cuuint64_t dims[5] = {1ull << a, 32ull, 1ull << (a2 - a - 5), 1ull << QB, 1ull << (n - a2 - QB)};
   const cuuint64_t strides[4] = {(1ull << a) * 8ull, (1ull << (a + 5)) * 8ull, (1ull << a2) * 8ull,
                                  (1ull << (a2 + QB)) * 8ull};
   const cuuint32_t box[5] = {1u << C, 32u, 1u, 1u << QB, 1u};
   const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<float2*>(psi), dims, strides, box, estr,
+  const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<float2*>(psi), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, l2_promotion(C),
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-static unsigned long long group_bits(int a, int a2, int q) {
-  return (((1ull << 5) - 1ull) << a) | (((1ull << (q - 5)) - 1ull) << a2);
-}
-
-template <int Q>
-static cudaError_t launch_corr_q(const LaunchCtx& lc, const float2* psi, int n, int a, int a2, int b, int b2,
-                                 double* partials, int nparts, int* err) {
-  constexpr int C = tma_c(Q);
-  using G = TmaGeom<Q, C>;
-  CUtensorMap m1, m2;
-  cudaError_t e = corr_map<Q>(psi, n, a, a2, &m1);
-  if (e != cudaSuccess) return e;
-  CorrWork cw{};
-  cw.a1[0] = a;
-  cw.a2[0] = a2;
-  long long nwork = 1ll << (n - Q - C);
-  if (b >= 0) {
-    const unsigned long long ga = group_bits(a, a2, Q), gb = group_bits(b, b2, Q);
-    if ((ga & gb) != 0ull || (ga | gb) != (((1ull << n) - 1ull) & ~((1ull << kLowBits) - 1ull)))
-      return cudaErrorInvalidValue;  // the two groups must partition [10, n)
-    e = corr_map<Q>(psi, n, b, b2, &m2);
-    if (e != cudaSuccess) return e;
-    cw.a1[1] = b;
-    cw.a2[1] = b2;
-    cw.cbits = kLowBits - C;
-    cw.na = cw.nb = 1ll << (n - kLowBits - Q);
-    nwork = (cw.na + cw.nb) << cw.cbits;
-  } else {
-    m2 = m1;
-    cw.a1[1] = a;
-    cw.a2[1] = a2;
-    cw.na = nwork;
-  }
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const long long ntiles = 1ll << (n - Q - C);
   auto kern = corr_tma_kernel<Q, C>;
-  e = allow_smem(reinterpret_cast<const void*>(kern), G::smem);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), G::smem);
   if (e != cudaSuccess) return e;
   long long grid = nparts;
-  if (grid > nwork) grid = nwork;
-  kern<<<static_cast<unsigned>(grid), G::NT, G::smem, lc.stream>>>(m1, m2, cw, nwork, partials, nparts, err);
+  if (grid > ntiles) grid = ntiles;
+  kern<<<static_cast<unsigned>(grid), G::NT, G::smem, lc.stream>>>(map, a, a2, ntiles, partials, nparts, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_corr_tma(const LaunchCtx& lc, const float2* psi, int n, int a, int a2, int q, double* partials,
-                            int nparts, int* err, int b, int b2) {
+                            int nparts, int* err) {
   switch (q) {
-    case 5: return launch_corr_q<5>(lc, psi, n, a, a2, b, b2, partials, nparts, err);
-    case 6: return launch_corr_q<6>(lc, psi, n, a, a2, b, b2, partials, nparts, err);
-    case 7: return launch_corr_q<7>(lc, psi, n, a, a2, b, b2, partials, nparts, err);
-    case 8: return launch_corr_q<8>(lc, psi, n, a, a2, b, b2, partials, nparts, err);
-    case 9: return launch_corr_q<9>(lc, psi, n, a, a2, b, b2, partials, nparts, err);
-    case 10: return launch_corr_q<10>(lc, psi, n, a, a2, b, b2, partials, nparts, err);
+    case 5: return launch_corr_q<5>(lc, psi, n, a, a2, partials, nparts, err);
+    case 6: return launch_corr_q<6>(lc, psi, n, a, a2, partials, nparts, err);
+    case 7: return launch_corr_q<7>(lc, psi, n, a, a2, partials, nparts, err);
+    case 8: return launch_corr_q<8>(lc, psi, n, a, a2, partials, nparts, err);
+    case 9: return launch_corr_q<9>(lc, psi, n, a, a2, partials, nparts, err);
+    case 10: return launch_corr_q<10>(lc, psi, n, a, a2, partials, nparts, err);
     default: return cudaErrorInvalidValue;
   }
 }

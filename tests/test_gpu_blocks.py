@@ -119,8 +119,7 @@ def check_state(torch, psi, o, ref, xs, prob_tol=PROB_TOL):
     assert abs(dp) <= prob_tol, (o["ground_prob"], ref.ground_prob())
     assert abs(o["norm"] - 1.0) <= NORM_TOL, o["norm"]
     assert o["ground_count"] == ref.ground_count()
-    # the correlation passes (one chunked launch for two groups up to n = 30)
-    # and the energy sum, against the blocks' oracle values; the FP32 state's
+    # the correlation passes and the energy sum, against the blocks' oracle values; the FP32 state's
     # error bounds them, not the reductions
     assert o["expect_hb"] == pytest.approx(ref.expect_hb(), rel=EXP_TOL, abs=EXP_TOL)
     assert o["expect_hp"] == pytest.approx(ref.expect_hp(), rel=EXP_TOL, abs=EXP_TOL)

@@ -238,8 +238,7 @@ def test_no_clauses_keeps_uniform(q, torch):
 
 
 # ---------------------------------------------------------------- observables
-# n = 22 and 24: the two equal correlation groups (6 + 6, 7 + 7 bits) run as one
-# chunked launch
+# n = 22 and 24: two strided correlation groups (6 + 6, 7 + 7 bits)
 @pytest.mark.parametrize("n", [1, 3, 10, 12, 17, 21, 22, 24])
 def test_observables_match_oracle(q, torch, n):
     cl = satgen.random_instance(n, 4 * n, seed=n, width=min(3, n))
