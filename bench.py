@@ -47,7 +47,7 @@ TRAFFIC = {
     # strided pass, 128-byte runs) on the 28-qubit instance with
     # QAA_GROUP_BITS=10,8: DRAM bytes read + written per launch for 2^28
     # amplitudes, scaled by the amplitude count (x4) to one 30-qubit launch.
-    "strided": {"bytes_per_launch": 4 * (2.147612e9 + 2.086614e9), "src_sha": "d62d7e870fb7b95c"},
+    "strided": {"bytes_per_launch": 4 * (2.147551e9 + 2.086624e9), "src_sha": "5f1e3ea4bd430d04"},
 }
 
 
