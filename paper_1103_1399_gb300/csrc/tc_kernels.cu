@@ -14,21 +14,19 @@
 // small addends added to a large accumulator) and are added in FP32 when read
 // back.
 //
-// A CTA (512 threads, one per SM) owns a tile of 8192 amplitudes in shared
+// A CTA (256 threads, one per SM) owns a tile of 8192 amplitudes in shared
 // memory: 2^Q rows of a strided group (Q <= 10) by 2^(13-Q) contiguous
 // amplitudes, loaded by a cp.async.bulk.tensor box; or, for the low pass
 // (bits 0..9), eight consecutive 1024-amplitude tiles loaded with cp.async.
 // Tile index u (13 bits): stage 1 takes its K from a 5-bit field of u and
 // stage 2 from u bits 8..12; the other 8 bits and re/im form 512 rows, four
-// M = 128 units (two per component).  Two threads share a row, each with half
-// of its 32 values (16 warps: lane quarter, row half, value half).  Per stage
-// each thread reads its 16 values (both components) from the tile, splits them
-// and writes the BF16 parts in the no-swizzle K-major core-matrix layout (8
-// rows x 16 bytes per core matrix, LBO = 128 B along K, SBO = 512 B along M);
-// one thread issues the MMAs (M = 128, N = 32, K = 16 each) and commits them
-// to an mbarrier; every thread then reads the 16 accumulator columns of its
-// half row with tcgen05.ld (its warp's lane quarter) and writes the results
-// back to the tile or, after the last stage,
+// M = 128 units (two per component).  Per stage each thread reads its row's 32
+// values from the tile, splits them and writes the BF16 parts in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
+// LBO = 128 B along K, SBO = 512 B along M); one thread issues the MMAs
+// (M = 128, N = 32, K = 16 each) and commits them to an mbarrier; every
+// thread then reads its row's accumulators with tcgen05.ld (its warp's lane
+// quarter) and writes the results back to the tile or, after the last stage,
 // straight to global memory.  The phases between transforms (the popcount
 // phase B, the merged P phase of the low pass, with the norm fold of the
 // previous step) are applied on the way.  The next tile's load is issued as
@@ -125,19 +123,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
-// 16 consecutive FP32 columns, as tmem_ld32
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // two FP32 values rounded to BF16 and packed (the first in the low half)
 __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
@@ -149,7 +134,7 @@ __device__ __forceinline__ float bf16_lo(uint32_t p) { return __uint_as_float(p 
 __device__ __forceinline__ float bf16_hi(uint32_t p) { return __uint_as_float(p & 0xffff0000u); }
 
 // ------------------------------------------------------------ geometry ------
-constexpr int kTcThreads = 512;
+constexpr int kTcThreads = 256;
 constexpr int kTcTile = 8192;          // amplitudes per CTA tile
 constexpr int kTcUnitBytes = 8192;     // one 128 x 32 BF16 operand unit
 constexpr int kTcCols = 256;           // tensor-memory columns: 4 units x (hi 32 + small 32)
@@ -223,12 +208,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* s_taddr = reinterpret_cast<uint32_t*>(bar_tma + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // warp w: tensor-memory lane quarter q4 (its rows within a unit), row half
-  // hh, and the half kh of each row's 32 values (K, and after the MMA N) it owns
-  const int q4 = warp & 3, hh = (warp >> 2) & 1, kh = warp >> 3;
+  const int q4 = warp & 3, hh = warp >> 2;
   const int r = 32 * q4 + lane;  // tensor-memory lane = row within a unit
   const int R = r + 128 * hh;    // row (without re/im), 0..255
-  const int k0 = 16 * kh;        // this thread's values k0 .. k0 + 15 of row R
 
   // tensor memory, barriers, the two Hadamard operands (K-major, N x K)
   if (warp == 0) tmem_alloc(s_taddr, kTcCols);
@@ -305,8 +287,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   for (long long T = blockIdx.x; T < ntiles; T += gridDim.x, ++it) {
     const unsigned long long xb = xbase_of(T);
     // energies of the low tile (stored per-tile counts, layout Y: lane = bits 5..9,
-    // register = bits 0..4): warp w < 8 expands 1024-tile w of the eight
-    if (LOW && warp < 8) {
+    // register = bits 0..4): warp w expands 1024-tile w of the eight
+    if (LOW) {
       unsigned pl[kPlanes];
       int nconst;
       load_counts(counts, T * 8 + warp, lane, pl, nconst);
@@ -328,34 +310,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       break;
     }
     pending = -1;
-    // kLpFirst: P before the transform (1024-tile j = warp & 7, lane = bits 0..4, k = bits 5..9)
+    // kLpFirst: P before the transform (warp = 1024-tile j, lane = bits 0..4, k = bits 5..9)
     if (KIND == kLpFirst) {
 #pragma unroll 4
-      for (int k = k0; k < k0 + 16; ++k) {
+      for (int k = 0; k < 32; ++k) {
         float2* p = s_t + tslot<LOW>(u_stage2(R, k));
-        *p = cmul(*p, s_pt[s_e[(warp & 7) * 32 * kTcEStride + k * kTcEStride + lane]]);
+        *p = cmul(*p, s_pt[s_e[warp * 32 * kTcEStride + k * kTcEStride + lane]]);
       }
       __syncthreads();
     }
     for (int w = 0; w < NW && !failed; ++w) {
       for (int st = TWO ? 1 : 2; st <= 2; ++st) {
-        // ---- A: this thread's half row, both components, split into BF16 parts
+        // ---- A: this thread's row, both components, split into BF16 parts
         {
-          float2 x[16];
+          float2 x[32];
 #pragma unroll
-          for (int k = 0; k < 16; ++k)
-            x[k] = s_t[tslot<LOW>(st == 1 ? u_stage1(R, k0 + k, C) : u_stage2(R, k0 + k))];
+          for (int k = 0; k < 32; ++k) x[k] = s_t[tslot<LOW>(st == 1 ? u_stage1(R, k, C) : u_stage2(R, k))];
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const int unit = 2 * hh + c;
 #pragma unroll
-            for (int kq = 0; kq < 2; ++kq) {
-              const int kb = 2 * kh + kq;  // 16-byte K chunk of the row (8 values)
+            for (int kb = 0; kb < 4; ++kb) {
               uint32_t ph[PARTS][4];
 #pragma unroll
               for (int t = 0; t < 4; ++t) {
-                float v0 = c ? x[8 * kq + 2 * t].y : x[8 * kq + 2 * t].x;
-                float v1 = c ? x[8 * kq + 2 * t + 1].y : x[8 * kq + 2 * t + 1].x;
+                float v0 = c ? x[8 * kb + 2 * t].y : x[8 * kb + 2 * t].x;
+                float v1 = c ? x[8 * kb + 2 * t + 1].y : x[8 * kb + 2 * t + 1].x;
 #pragma unroll
                 for (int p = 0; p < PARTS; ++p) {
                   const uint32_t b = bf16x2(v0, v1);
@@ -406,18 +386,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           break;
         }
         tc_fence_after();
-        // ---- read back: y[k'] for this thread's half row (k' = k0 + k), both components
-        float2 y[16];
+        // ---- read back: y[k'] for this row, both components
+        float2 y[32];
         {
-          float hi[16], sm[16];
-          tmem_ld16(t_row + (2 * hh) * 64 + k0, hi);
-          tmem_ld16(t_row + (2 * hh) * 64 + 32 + k0, sm);
+          float hi[32], sm[32];
+          tmem_ld32(t_row + (2 * hh) * 64, hi);
+          tmem_ld32(t_row + (2 * hh) * 64 + 32, sm);
 #pragma unroll
-          for (int k = 0; k < 16; ++k) y[k].x = hi[k] + sm[k];
-          tmem_ld16(t_row + (2 * hh + 1) * 64 + k0, hi);
-          tmem_ld16(t_row + (2 * hh + 1) * 64 + 32 + k0, sm);
+          for (int k = 0; k < 32; ++k) y[k].x = hi[k] + sm[k];
+          tmem_ld32(t_row + (2 * hh + 1) * 64, hi);
+          tmem_ld32(t_row + (2 * hh + 1) * 64 + 32, sm);
 #pragma unroll
-          for (int k = 0; k < 16; ++k) y[k].y = hi[k] + sm[k];
+          for (int k = 0; k < 32; ++k) y[k].y = hi[k] + sm[k];
         }
         if (st == 2) {
           // phases due after a whole transform: B between the two transforms of
@@ -425,22 +405,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (KIND == kSpWBW && w == 0) {
             const int pc0 = __popcll(xb);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const int u = u_stage2(R, k0 + k);
+            for (int k = 0; k < 32; ++k) {
+              const int u = u_stage2(R, k);
               y[k] = cmul(y[k], s_bt[pc0 + __popc(u & ((1 << C) - 1)) + __popc(u >> C)]);
             }
           }
           if ((KIND == kLpMerge && w == 0) || KIND == kLpLast) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-              y[k] = cmul(y[k], s_pt[s_e[(warp & 7) * 32 * kTcEStride + (k0 + k) * kTcEStride + lane]]);
+            for (int k = 0; k < 32; ++k) y[k] = cmul(y[k], s_pt[s_e[warp * 32 * kTcEStride + k * kTcEStride + lane]]);
           }
         }
         if (w == NW - 1 && st == 2) {
           // to global memory (x of u = R | k << 8)
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int u = u_stage2(R, k0 + k);
+          for (int k = 0; k < 32; ++k) {
+            const int u = u_stage2(R, k);
             unsigned long long x;
             if (LOW) {
               x = xb + static_cast<unsigned long long>((u & 31) | ((u >> 8) << 5) | (((u >> 5) & 7) << 10));
@@ -454,13 +433,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (LOW && nf.out) {
             float t = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) t = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, t));
+            for (int k = 0; k < 32; ++k) t = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, t));
             nacc = df_add1(nacc, t);
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < 16; ++k)
-            s_t[tslot<LOW>(st == 1 ? u_stage1(R, k0 + k, C) : u_stage2(R, k0 + k))] = y[k];
+          for (int k = 0; k < 32; ++k) s_t[tslot<LOW>(st == 1 ? u_stage1(R, k, C) : u_stage2(R, k))] = y[k];
         }
         tc_fence_before();
         __syncthreads();
