@@ -281,7 +281,6 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NT, (TmaGeom<Q, C>::NT >= 512 ?
 constexpr int kLpRowT = 33;
 constexpr int kLpSlotsT = 32 * kLpRowT;
 constexpr int kLpTmaWarps = 8;
-constexpr int kLpSplitDefault = 0;  // warps per CTA of the split-buffer low pass by default (0: off)
 
 struct LpTmaLayout {
   size_t off_pt, off_warp, per_warp, off_bar, total;
@@ -291,23 +290,6 @@ struct LpTmaLayout {
     per_warp = (8u * kLpSlotsT + 8u * static_cast<size_t>(m + 16) + 127u) & ~static_cast<size_t>(127);
     off_bar = off_warp + per_warp * kLpTmaWarps;
     total = off_bar + 8u * kLpTmaWarps;
-  }
-};
-
-// Split buffers (merged passes with stored counts): each warp has a landing
-// buffer for its tile's bulk copy and a separate padded transpose buffer, so
-// that the next tile's copy is issued as soon as the current tile is in
-// registers and each warp keeps a copy in flight while it computes.  No clause
-// table or active-clause list (the counts are stored): P row, then per warp
-// 8 KiB + 8.25 KiB.  nw warps per CTA: 6 (two CTAs per SM) or 13 (one).
-struct LpSplitLayout {
-  size_t off_pt, off_warp, per_warp, off_bar, total;
-  __host__ __device__ LpSplitLayout(int m, int nw) {
-    off_pt = 0;
-    off_warp = (8u * static_cast<size_t>(m + 1) + 127u) & ~static_cast<size_t>(127);
-    per_warp = 8192u + 8u * kLpSlotsT;
-    off_bar = off_warp + per_warp * nw;
-    total = off_bar + 8u * nw;
   }
 };
 
@@ -383,31 +365,24 @@ __device__ __forceinline__ void quad_rot2(float2* const (&b)[4], const float2 (&
   }
 }
 
-// NW: warps per CTA; NW != kLpTmaWarps selects the split buffers (stored
-// counts required, not for kLpRot12).
-template <int KIND, int NW>
-__global__ void __launch_bounds__(NW * 32, (NW <= kLpTmaWarps ? 2 : 1))
+template <int KIND>
+__global__ void __launch_bounds__(kLpTmaWarps * 32, 2)
     lp_tma_kernel(float2* __restrict__ psi, int m, const ClauseLP* __restrict__ cl, const float2* __restrict__ prow,
                   const float2* __restrict__ brow, int n, long long ntiles, int* __restrict__ err,
                   const unsigned* __restrict__ counts, const NormFold nf) {
   constexpr bool kRegLow = KIND != kLpFirst && KIND != kLpPhase;  // phase applied in layout Y
-  constexpr bool kSplit = NW != kLpTmaWarps;
   extern __shared__ __align__(1024) unsigned char smem[];
-  const LpTmaLayout L0(m);
-  const LpSplitLayout L1(m, NW);
-  const size_t off_pt = kSplit ? L1.off_pt : L0.off_pt, off_warp = kSplit ? L1.off_warp : L0.off_warp,
-               per_warp = kSplit ? L1.per_warp : L0.per_warp, off_bar = kSplit ? L1.off_bar : L0.off_bar;
+  const LpTmaLayout L(m);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   ClauseLP* s_cl = reinterpret_cast<ClauseLP*>(smem);
-  float2* s_pt = reinterpret_cast<float2*>(smem + off_pt);
-  unsigned char* wbase = smem + off_warp + per_warp * warp;
-  float2* s_buf = reinterpret_cast<float2*>(wbase);  // dense tile (and, unless split, the padded transposes)
-  float2* s_xp = kSplit ? reinterpret_cast<float2*>(wbase + 8192u) : s_buf;
+  float2* s_pt = reinterpret_cast<float2*>(smem + L.off_pt);
+  unsigned char* wbase = smem + L.off_warp + L.per_warp * warp;
+  float2* s_buf = reinterpret_cast<float2*>(wbase);  // dense tile, then padded transposes
   uint2* s_act = reinterpret_cast<uint2*>(wbase + 8u * kLpSlotsT);
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + off_bar) + warp;
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp;
 
-  const long long step = static_cast<long long>(gridDim.x) * NW;
-  const long long first = static_cast<long long>(blockIdx.x) * NW + warp;
+  const long long step = static_cast<long long>(gridDim.x) * kLpTmaWarps;
+  const long long first = static_cast<long long>(blockIdx.x) * kLpTmaWarps + warp;
   if (lane == 0) {
     mbar_init(s_bar, 1);
     fence_mbar_init();
@@ -417,8 +392,7 @@ __global__ void __launch_bounds__(NW * 32, (NW <= kLpTmaWarps ? 2 : 1))
     mbar_expect_tx(s_bar, 8192u);
     bulk_load(s_buf, psi + (first << kLowBits), 8192u, s_bar);
   }
-  if (!kSplit)
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s_cl[i] = cl[i];
   // the rotation form's last pass of a step also removes the 2^n of its rotations (exact)
   constexpr bool kRot = KIND == kLpRot || KIND == kLpRot12;
   constexpr bool kQuad = KIND == kLpRot12;
@@ -437,7 +411,7 @@ __global__ void __launch_bounds__(NW * 32, (NW <= kLpTmaWarps ? 2 : 1))
   float2* qbuf[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k)
-    qbuf[k] = reinterpret_cast<float2*>(smem + off_warp + per_warp * (4 * quad + k));
+    qbuf[k] = reinterpret_cast<float2*>(smem + L.off_warp + L.per_warp * (4 * quad + k));
   __syncthreads();
 
   int nconst = 0, npad = 0;
@@ -473,37 +447,31 @@ __global__ void __launch_bounds__(NW * 32, (NW <= kLpTmaWarps ? 2 : 1))
       for (int r = 0; r < 32; ++r) v[r] = src[32 * r];
     }
     __syncwarp();
-    const long long tn = tile + step;
-    if (kSplit && lane == 0 && tn < ntiles) {
-      // the landing buffer is free already: the next tile's copy overlaps all of this one
-      fence_proxy_async();
-      mbar_expect_tx(s_bar, 8192u);
-      bulk_load(s_buf, psi + (tn << kLowBits), 8192u, s_bar);
-    }
     if (KIND == kLpPhase) {
       apply_p_phase(v, pl, nconst, s_pt);
     } else if (kRot) {
       reg_rot<5>(v, rtab);
-      xpose_x2y_t(v, s_xp, lane);
+      xpose_x2y_t(v, s_buf, lane);
       reg_rot<5>(v, rtab);
       apply_p_phase(v, pl, nconst, s_pt);
-      xpose_y2x_t(v, s_xp, lane);
+      xpose_y2x_t(v, s_buf, lane);
     } else if (KIND == kLpFirst) {
       apply_p_phase(v, pl, nconst, s_pt);
       reg_wht<0, 5>(v);
-      xpose_x2y_t(v, s_xp, lane);
+      xpose_x2y_t(v, s_buf, lane);
       reg_wht<0, 5>(v);
-      xpose_y2x_t(v, s_xp, lane);
+      xpose_y2x_t(v, s_buf, lane);
     } else {
       reg_wht<0, 5>(v);
-      xpose_x2y_t(v, s_xp, lane);
+      xpose_x2y_t(v, s_buf, lane);
       reg_wht<0, 5>(v);
       apply_p_phase(v, pl, nconst, s_pt);
       if (KIND == kLpMerge) reg_wht<0, 5>(v);
-      xpose_y2x_t(v, s_xp, lane);
+      xpose_y2x_t(v, s_buf, lane);
       if (KIND == kLpMerge) reg_wht<0, 5>(v);
     }
-    if (!kSplit && lane == 0 && tn < ntiles) {
+    const long long tn = tile + step;
+    if (lane == 0 && tn < ntiles) {
       fence_proxy_async();
       mbar_expect_tx(s_bar, 8192u);
       bulk_load(s_buf, psi + (tn << kLowBits), 8192u, s_bar);
@@ -843,51 +811,26 @@ cudaError_t launch_lp_counts(const LaunchCtx& lc, unsigned* counts, int n, int m
   return cudaGetLastError();
 }
 
-template <int KIND, int NW>
-static cudaError_t launch_lp_tma_nw(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl,
-                                    const float2* prow, const float2* brow, int* err, const unsigned* counts,
-                                    const NormFold& nf) {
-  const long long ntiles = 1ll << (n - kLowBits);
-  constexpr bool split = NW != kLpTmaWarps;
-  const size_t smem = split ? LpSplitLayout(m, NW).total : LpTmaLayout(m).total;
-  const size_t smem_max = split ? LpSplitLayout(QAA_MAX_CLAUSES_DEV, NW).total : LpTmaLayout(QAA_MAX_CLAUSES_DEV).total;
-  auto kern = lp_tma_kernel<KIND, NW>;
-  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), smem_max);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NW * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
-  long long grid = static_cast<long long>(occ) * lc.num_sms;
-  const long long need = (ntiles + NW - 1) / NW;
-  if (grid > need) grid = need;
-  if (grid > kFoldSlot - 1) grid = kFoldSlot - 1;  // one norm-fold partial per CTA
-  kern<<<static_cast<unsigned>(grid), NW * 32, smem, lc.stream>>>(psi, m, cl, prow, brow, n, ntiles, err, counts, nf);
-  return cudaGetLastError();
-}
-
-// Warps per CTA of the split-buffer low pass (0: off): QAA_LP_SPLIT = 0, 6 or 13.
-static int lp_split_warps() {
-  static const int w = [] {
-    const char* v = std::getenv("QAA_LP_SPLIT");
-    const int x = v ? std::atoi(v) : kLpSplitDefault;
-    return (x == 6 || x == 13) ? x : 0;
-  }();
-  return w;
-}
-
 template <int KIND>
 static cudaError_t launch_lp_tma(const LaunchCtx& lc, float2* psi, int n, int m, const ClauseLP* cl,
                                  const float2* prow, const float2* brow, int* err, const unsigned* counts,
                                  const NormFold& nf) {
-  // the split buffers need the stored counts (no clause table or active list)
-  if constexpr (KIND == kLpRot || KIND == kLpMerge || KIND == kLpLast) {
-    if (counts) {
-      if (lp_split_warps() == 6) return launch_lp_tma_nw<KIND, 6>(lc, psi, n, m, cl, prow, brow, err, counts, nf);
-      if (lp_split_warps() == 13) return launch_lp_tma_nw<KIND, 13>(lc, psi, n, m, cl, prow, brow, err, counts, nf);
-    }
-  }
-  return launch_lp_tma_nw<KIND, kLpTmaWarps>(lc, psi, n, m, cl, prow, brow, err, counts, nf);
+  const long long ntiles = 1ll << (n - kLowBits);
+  const LpTmaLayout L(m);
+  auto kern = lp_tma_kernel<KIND>;
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(kern), LpTmaLayout(QAA_MAX_CLAUSES_DEV).total);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLpTmaWarps * 32, L.total);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  long long grid = static_cast<long long>(occ) * lc.num_sms;
+  const long long need = (ntiles + kLpTmaWarps - 1) / kLpTmaWarps;
+  if (grid > need) grid = need;
+  if (grid > kFoldSlot - 1) grid = kFoldSlot - 1;  // one norm-fold partial per CTA
+  kern<<<static_cast<unsigned>(grid), kLpTmaWarps * 32, L.total, lc.stream>>>(psi, m, cl, prow, brow, n, ntiles,
+                                                                              err, counts, nf);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pass_tma(const LaunchCtx& lc, const Pass& p, float2* psi, int n, int m, const ClauseLP* cl,
