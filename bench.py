@@ -694,6 +694,40 @@ def run_ours(args):
         torch.cuda.empty_cache()
         psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
 
+    # the largest state one GPU holds: n = 34 (128 GiB, plus 22 GiB of stored
+    # per-tile counts), a random 3-SAT instance at ratio 4.2 (m = 143), a short
+    # run; only with --n34
+    n34 = None
+    if args.n34 and rank == 0:
+        psi = None
+        torch.cuda.empty_cache()
+        free, _ = torch.cuda.mem_get_info()
+        if free >= 160 << 30:
+            c34 = satgen.random_instance(34, 143, seed=0, width=3)
+            p34 = torch.empty(1 << 34, dtype=torch.complex64, device="cuda")
+            i34 = q.Instance(34, c34, stream=stream)
+            k34 = 6
+            i34.init_uniform(p34)
+            i34.evolve(p34, DT * 2, 2)
+            torch.cuda.synchronize()
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            i34.evolve(p34, DT * k34, k34)
+            h1.record(stream)
+            torch.cuda.synchronize()
+            ms34 = h0.elapsed_time(h1)
+            rts = round_trips(i34.describe_plan())
+            n34 = {"steps_per_s": k34 / (ms34 / 1e3), "ms_per_step": ms34 / k34, "steps": k34,
+                   "plan": i34.describe_plan(), "m": len(c34),
+                   "hbm_gbs": rts * 2 * 8 * (1 << 34) * k34 / (ms34 / 1e3) / 1e9,
+                   "instance": "uniform random 3-SAT, ratio 4.2, seed 0 (timing only)"}
+            i34.close()
+            del p34
+        else:
+            n34 = {"skipped": f"needs 160 GiB free, {free / 2**30:.0f} GiB free"}
+        torch.cuda.empty_cache()
+        psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+
     # the small configurations: n = 12 (T = 20, seeds 0..9, on chip) and n = 20
     # (T = 10, 40, 160; the 8 MiB state is L2-resident), dt = 0.05
     small = None
@@ -753,6 +787,7 @@ def run_ours(args):
             "order4": order4,
             "small_configs": small,
             "n32": n32,
+            "n34": n34,
             "serving": serving,
             "cpu_baseline": cpu,
             "final": {"norm": obs["norm"], "ground_prob": obs["ground_prob"]},
@@ -779,6 +814,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip timing the tensor-core WHT variants and the launch-graph mode")
     ap.add_argument("--no-n32", action="store_true", help="skip the short 32-qubit (32 GiB) run")
+    ap.add_argument("--n34", action="store_true", help="add a short 34-qubit run (128 GiB state)")
     ap.add_argument("--no-small", action="store_true", help="skip the n=12 and n=20 configuration lines")
     ap.add_argument("--no-spectrum", action="store_true", help="skip the Lanczos spectrum lines")
     ap.add_argument("--serving-requests", type=int, default=1024,
