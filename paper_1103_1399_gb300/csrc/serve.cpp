@@ -209,6 +209,7 @@ struct qaa_server {
   // makes one request's steps faster but several n = 20..22 requests then
   // contend for L2 and HBM at once.
   bool use_graphs = false;
+  int graph_max_bits = 0;  // streamed requests with n <= this run as one launch graph
   // small-request batches
   cudaStream_t batch_stream = nullptr;
   qaa::OnchipJob* h_jobs[2] = {nullptr, nullptr};
@@ -652,6 +653,7 @@ qaa_status qaa_server_create(size_t hbm_budget_bytes, int max_slots, qaa_server*
   if (const char* v = std::getenv("QAA_PERSIST_MAX_BITS")) s->persist_max_bits = std::min(std::atoi(v), qaa::kPersistMaxBits);
   if (const char* v = std::getenv("QAA_PERSIST_GRID")) s->persist_grid = std::max(1, std::atoi(v));
   if (const char* v = std::getenv("QAA_SERVER_GRAPHS")) s->use_graphs = std::atoi(v) != 0;
+  if (const char* v = std::getenv("QAA_SERVER_GRAPH_BITS")) s->graph_max_bits = std::atoi(v);
   if (cudaMallocHost(&s->h_res, sizeof(double) * 8 * max_slots) != cudaSuccess ||
       cudaMallocHost(&s->h_stage, kStageBytes * static_cast<size_t>(max_slots)) != cudaSuccess)
     return bail(QAA_E_NOMEM, "cannot allocate result slots");
@@ -727,7 +729,7 @@ qaa_status qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, doubl
     qaa::make_plan(n, r->plan, 10);  // the persistent kernel's tiles hold at most 10 bits
     qaa::narrow_low_pass(r->plan, 10);
   }
-  r->graph = !r->plan.onchip && !r->persist && s->use_graphs;
+  r->graph = !r->plan.onchip && !r->persist && (s->use_graphs || n <= s->graph_max_bits);
   // Streamed requests store the per-tile clause counts once (1.375 bytes per
   // amplitude) so the merged low passes read them instead of counting each step.
   {
