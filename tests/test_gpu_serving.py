@@ -80,6 +80,31 @@ def test_same_result_alone_and_in_the_mix(env):
     assert stats["streamed_requests"] == sum(1 for n, *_ in MIX if n > 14)
 
 
+def test_streamed_requests_as_launch_graphs_are_bit_identical(env, monkeypatch):
+    """QAA_SERVER_GRAPH_BITS (read when the server is created) runs streamed
+    requests up to that size as one launch graph each: the same kernels in the
+    same order with the same phase rows and norm-fold slots, so the same
+    results bit for bit as per-pass launches."""
+    q, _ = env
+    reqs = [(18, 31, 2.0, 40), (20, 32, 1.0, 19), (21, 33, 1.0, 9)]
+    insts = {seed: satgen.planted_instance(n, seed)["clauses"] for n, seed, _, _ in reqs}
+    keys = ("success_prob", "norm", "energy", "expect_hb", "ground_count")
+
+    def serve():
+        with q.Server(max_slots=8) as srv:
+            tickets = [srv.submit(n, insts[seed], T, K) for n, seed, T, K in reqs]
+            res = wait_all(srv, tickets)
+        return [res[t] for t in tickets]
+
+    monkeypatch.delenv("QAA_SERVER_GRAPH_BITS", raising=False)
+    plain = serve()
+    monkeypatch.setenv("QAA_SERVER_GRAPH_BITS", "22")
+    graphs = serve()
+    for a, b in zip(plain, graphs):
+        assert a["status"] == b["status"] == 0
+        assert all(a[k] == b[k] for k in keys), (a, b)
+
+
 @pytest.mark.parametrize("n,T,K", [(15, 3.0, 20), (16, 2.0, 16), (19, 2.0, 8), (21, 1.0, 4)])
 def test_persistent_requests_match_oracle(env, n, T, K, monkeypatch):
     q, _ = env
