@@ -124,7 +124,7 @@ def _ptr(x):
 
 
 def tune_candidates(n):
-    """Round-1 autotune candidates for n, as plan descriptions (qaa_tune_candidates; no GPU needed)."""
+    """Stage-1 autotune candidates for n, as plan descriptions (qaa_tune_candidates; no GPU needed)."""
     buf = ctypes.create_string_buffer(1 << 20)
     count = lib.qaa_tune_candidates(int(n), buf, len(buf))
     if count < 0:
