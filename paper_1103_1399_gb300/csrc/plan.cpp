@@ -254,6 +254,19 @@ void make_default_plan(int n, PassPlan& plan, int max_q, int low) {
     plan.strided[0] = {L, q, L + q + 5};
     plan.strided[1] = {L + 5, q, L + 10};
   }
+  // Three groups at n = 33..34 (23..24 strided bits): contiguous 8-bit groups
+  // put rows up to 512 MiB apart, 256 memory pages per tile.  Instead an 11-bit
+  // group {L..L+4} + the top 6 bits, and the bits between in two contiguous
+  // groups: at most 64 pages per tile.
+  if (split && plan.strided.size() == 3 && max_q >= 11 && n >= 33 && L == kLowBits) {
+    const int mid = n - 6 - (L + 5);  // bits [L+5, n-6) for the other two groups
+    const int q1 = (mid + 1) / 2, q2 = mid - q1;
+    if (q2 >= 5) {
+      plan.strided[0] = {L, 11, n - 6};
+      plan.strided[1] = {L + 5, q1, L + 10};
+      plan.strided[2] = {L + 5 + q1, q2, L + 10 + q1};
+    }
+  }
   const int ng = static_cast<int>(plan.strided.size());
   plan.phase_group = ng - 1;
   if (const char* pg = std::getenv("QAA_PHASE_GROUP")) {

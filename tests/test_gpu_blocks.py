@@ -242,7 +242,8 @@ def test_block_instance_n32(env):
 def test_block_instance_largest_states(env, n):
     """The largest states one GB300 holds: 2^33 and 2^34 amplitudes (64 and
     128 GiB, plus 11 and 22 GiB of stored per-tile counts), three strided
-    groups and 4 HBM round trips per step, 40 steps of the benchmark's dt."""
+    groups (an 11-bit one with the top bits) and 4 HBM round trips per step,
+    40 steps of the benchmark's dt."""
     q, torch = env
     inst = satgen.block_instance(n, 3, 160, 180, seed=11 + n)
     K = 40
@@ -255,6 +256,8 @@ def test_block_instance_largest_states(env, n):
             h.evolve(psi, DT * K, K)
             o = h.observables(psi)
         assert "rotation form" in plan and plan.count("group bits") == 3, plan
+        # the 11-bit group with the top 6 bits: at most 64 memory pages per tile
+        assert f"group bits [10,15)+[{n - 6},{n})" in plan, plan
         check_state(torch, psi, o, ref, sample_points(inst, n, 6))
     finally:
         del psi
