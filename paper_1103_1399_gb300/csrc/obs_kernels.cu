@@ -16,7 +16,7 @@
 //   * E |psi|^2: the same split of E times the FP32 part;
 //   * each lane's running sums over its 32 amplitudes of a tile: TwoSum into a
 //     (sum, error) pair, on packed f32x2 instructions for (norm, <H_P>);
-//   * once per tile the pairs are added into the lane's FP64 totals.
+//   * once per four tiles the pairs are added into the lane's FP64 totals.
 // The result agrees with exact-product FP64 sums to about 1e-14 relative.
 // The pair correlations C (n pair products per amplitude) are formed and
 // summed in FP32 over one thread's share of one tile (at most 320 products)
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kObsWarps * 32, 2)
     ObsAddUnroll<0>::run(a, v, pl, nconst, lane, 1 << kLowBits);
     const float2 c = bits_f2(c2);
     d_corr += static_cast<double>(c.x + c.y);
-    if ((it & 1) || tn >= ntiles) {
+    if ((it & 3) == 3 || tn >= ntiles) {
       const float2 ss = bits_f2(a.s), ee = bits_f2(a.e);
       d_norm += static_cast<double>(ss.x) + static_cast<double>(ee.x);
       d_hp += static_cast<double>(ss.y) + static_cast<double>(ee.y);
