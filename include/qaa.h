@@ -214,13 +214,15 @@ qaa_status qaa_init_uniform(qaa_handle h, void* psi);
  * `steps` Strang steps (dt = T/steps), Eq. (1) with the linear sweep s = t/T.
  * T >= 0, steps >= 1.  Asynchronous on the handle's stream.
  * For n >= 15 on the TMA passes the handle stores, on the first evolution,
- * the bit-sliced violated-clause counts of every 1024-amplitude tile (1.375
- * bytes per amplitude: 1.4 GiB at n = 30) so that later low passes read them
+ * the bit-sliced violated-clause counts of every 1024-amplitude tile (as many
+ * bit planes as the instance's largest count needs, at most 10: 1.25 bytes
+ * per amplitude, 0.88 for the 30-qubit benchmark instance), allocated once at
+ * the largest size (1.25 GiB at n = 30), so that later low passes read them
  * instead of counting again; if that memory cannot be allocated the passes
  * count on the fly (the same values).  QAA_LP_COUNTS=0 turns the store off.
  * Norm fold: the exact evolution is unitary, and the low passes measure the
  * FP32 state's norm (|psi|^2 summed in the pass, no extra read; every step for
- * n >= 22, every 8 steps below) so that the next one scales its phase row
+ * n >= 26, every 2, 4 or 8 steps below) so that a later one scales its phase row
  * back to the norm psi had at the start of the call (times the exact power of
  * two of the unnormalised transforms): the norm stays within about 1e-7 of
  * its starting value instead of drifting with the roundings (about 4e-6

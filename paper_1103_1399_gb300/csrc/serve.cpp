@@ -730,8 +730,9 @@ qaa_status qaa_submit(qaa_server* s, int n, const int32_t* clauses, int m, doubl
     qaa::narrow_low_pass(r->plan, 10);
   }
   r->graph = !r->plan.onchip && !r->persist && (s->use_graphs || n <= s->graph_max_bits);
-  // Streamed requests store the per-tile clause counts once (1.375 bytes per
-  // amplitude) so the merged low passes read them instead of counting each step.
+  // Streamed requests store the per-tile clause counts once (at most 1.25
+  // bytes per amplitude) so the merged low passes read them instead of
+  // counting each step.
   {
     const char* env = std::getenv("QAA_LP_COUNTS");
     if (!r->plan.onchip && !r->persist && r->plan.use_tma && n > qaa::kOnchipMaxBits && !(env && std::atoi(env) == 0))
